@@ -1,0 +1,220 @@
+/*
+ * mppi.h -- C ABI of the GB300 MPPI library (libmppi_gb300.so).
+ *
+ * One call solves one MPPI optimisation step of "Model Predictive Path
+ * Integral Control for Agile Unmanned Aerial Vehicles" (arXiv 2407.09812):
+ * sample K perturbed control sequences (Sec. III-A, Eq. rollout_computation),
+ * roll each out through the quadrotor model with its motor constraints over
+ * N steps (Sec. III-B), score it with the tracking / input / obstacle cost
+ * (Sec. IV-C, Sec. IV-D), weight the samples by the softmin of Eq. cost_2
+ * and return the updated nominal sequence of Eq. u_update together with the
+ * command sent to the low-level controller and the shifted warm start
+ * (Alg. 1).
+ *
+ * Layouts (all float32, row major, no padding):
+ *   state     x[13]      = p(3) [m], q(4) = (w, x, y, z) unit quaternion
+ *                          rotating body to world, v(3) [m/s], omega(3)
+ *                          body rates [rad/s]; world z up, gravity -z.
+ *   control   u[4]       = F_t [N], omega_d(3) [rad/s] desired body rates.
+ *   reference ref[N+1][13]  x_ref_0 .. x_ref_N, same layout as a state.
+ *   nominal   u_nom[N][4]
+ *   obstacle  obs[M][4]  = (cx, cy, cz, r); r >= 0 a sphere of radius r,
+ *                          r < 0 a vertical infinite cylinder of radius |r|
+ *                          (cz unused).  The pointer must be 16-byte
+ *                          aligned (it is staged with bulk copies).
+ *
+ * Ownership: the caller owns every buffer it passes; the library never
+ * keeps a caller pointer beyond the call (synchronous entry points) or
+ * beyond completion of the work enqueued on the given stream
+ * (asynchronous entry points).  A handle owns its device workspace.
+ *
+ * Errors: every entry point returns MPPI_OK (0) or a negative code.
+ * Arguments are validated on the host before any device work is queued;
+ * on MPPI_EINVAL nothing is written.  Handles are not thread safe; a
+ * server (mppi_server_*) is.  No entry point throws or aborts.
+ */
+#ifndef MPPI_GB300_H
+#define MPPI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPPI_OK 0
+#define MPPI_EINVAL (-1)     /* bad size, pointer, alignment or parameter   */
+#define MPPI_ENOMEM (-2)     /* device memory or admission budget exceeded  */
+#define MPPI_ECUDA (-3)      /* a CUDA runtime call failed                  */
+#define MPPI_ETIMEOUT (-4)   /* a bounded device-side wait gave up          */
+#define MPPI_ENONFINITE (-5) /* every rollout cost was non-finite           */
+#define MPPI_EAGAIN (-6)     /* queue full / nothing ready; retry later     */
+#define MPPI_ENOTFOUND (-7)  /* unknown vehicle or request id               */
+
+#define MPPI_N_MAX 1024      /* largest horizon N                            */
+#define MPPI_M_MAX 8192      /* largest obstacle count M per instance        */
+#define MPPI_K_MAX (1 << 24) /* largest sample count K per instance          */
+
+/* Vehicle model and input limits (Table I of the paper; Sec. III-B). */
+typedef struct {
+    float mass;        /* m [kg]                                            */
+    float g;           /* |g| [m/s^2]                                       */
+    float arm_l;       /* arm length l [m] (allocation matrix Gamma)        */
+    float c_tf;        /* rotor torque constant c_tf [m]                    */
+    float J[3];        /* diagonal inertia [kg m^2]                         */
+    float T_min;       /* per-rotor thrust limits [N] (Eq. clipping)        */
+    float T_max;
+    int32_t motor_clip;/* 1: clip rotor thrusts; 0: no rotor limits        */
+    float F_min;       /* box on the desired collective thrust [N]          */
+    float F_max;
+    float w_max[3];    /* box on the desired body rates [rad/s] (Sec. IV)   */
+} mppi_model;
+
+/* Optimiser and cost parameters (Table II; Sec. IV-C, IV-D). */
+typedef struct {
+    int32_t K;         /* rollouts                                          */
+    int32_t N;         /* prediction steps                                  */
+    float dt;          /* prediction time step [s]                          */
+    float lambda;      /* temperature of Eq. cost_2, > 0                    */
+    float sigma[4];    /* noise standard deviation per control component    */
+    float c_p, c_q, c_v, c_w;  /* Eq. rho_ref weights                       */
+    float R[4];        /* input weight diagonal (Eq. cost)                  */
+    float Rd[4];       /* input-change weight diagonal (Eq. cost)           */
+    float c_obs;       /* collision indicator weight (Sec. IV-D)            */
+    float c_bar;       /* exponential barrier weight                        */
+    float beta;        /* barrier rate [1/m^2]: c_bar exp(-beta max(gap,0)) */
+    float r_uav;       /* vehicle radius added to every obstacle [m]        */
+    int32_t quat_metric; /* 0: 1-<q,q_ref>^2 (Eq. quat_approx);
+                            1: acos(2<q,q_ref>^2-1) (Eq. quat_angle)        */
+    int32_t tail_mode; /* warm start tail: 0 hover u_init, 1 repeat last    */
+    float shift_alpha; /* 1: shift by one step (Alg. 1); in (0,1): linear
+                          interpolation alpha steps later (Sec. IV-B)       */
+    float delay;       /* >= 0 [s]: start the rollouts from x_hat predicted
+                          `delay` ahead (delay compensation, Sec. IV-E)     */
+    uint64_t seed;     /* Philox key (with stream_id)                       */
+    uint32_t stream_id;
+    int32_t reserved;  /* must be 0                                         */
+} mppi_params;
+
+/* Capacity of a handle's device workspace. */
+typedef struct {
+    int32_t max_instances; /* instances per batched launch (>= 1)           */
+    int64_t max_samples;   /* sum of K over one batched launch              */
+    int32_t N_max;         /* largest N of any instance                     */
+    int32_t M_max;         /* largest M of any instance                     */
+} mppi_capacity;
+
+typedef struct mppi_ctx* mppi_handle;
+
+/* Library version and the error string of a code (static storage). */
+const char* mppi_version(void);
+const char* mppi_strerror(int code);
+
+/* Creates a handle for one vehicle model and one parameter set on the
+ * current CUDA device; allocates its device workspace for `cap` (NULL:
+ * one instance of params->K, params->N, MPPI_M_MAX obstacles).
+ * Returns MPPI_EINVAL for non-finite or out-of-range values, MPPI_ENOMEM
+ * or MPPI_ECUDA if the workspace cannot be allocated. */
+int mppi_create(const mppi_model* model, const mppi_params* params, const mppi_capacity* cap,
+                mppi_handle* out);
+
+/* Frees the handle and its workspace (synchronises its device work). */
+void mppi_destroy(mppi_handle h);
+
+/* Replaces the parameter set (K and N within the capacity).  Takes effect
+ * for calls made afterwards. */
+int mppi_set_params(mppi_handle h, const mppi_params* params);
+
+/* One MPPI step with HOST buffers, synchronous (Alg. 1, body of the loop).
+ *   x_hat[13]          state estimate x^ (host).
+ *   ref[(N+1)*13]      reference x_ref_0..x_ref_N (host).
+ *   obstacles[M*4]     obstacle set (host, may be NULL when M == 0).
+ *   u_nom[N*4]         nominal sequence before the update (host).
+ *   iter               Philox counter word of this step (advance per step).
+ * Outputs (host, each may be NULL):
+ *   u_out[N*4]   updated nominal u_nom_j + sum_k w_k delta u_j^k (Eq. u_update),
+ *                before the shift;
+ *   u_cmd[4]     [F_clip, omega_clip] from x_hat and u_out_0 (Sec. III-B);
+ *   u_next[N*4]  warm start for the next step (shift / interpolation);
+ *   x_next[13]   x_hat advanced by the applied command over shift_alpha*dt;
+ *   costs[K]     per-sample cost S_k.
+ * Returns MPPI_OK, MPPI_EINVAL, MPPI_ECUDA, MPPI_ETIMEOUT, or
+ * MPPI_ENONFINITE (every S_k non-finite: u_out = u_nom). */
+int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float* obstacles, int32_t M,
+               const float* u_nom, uint64_t iter, float* u_out, float* u_cmd, float* u_next,
+               float* x_next, float* costs);
+
+/* The same step with DEVICE buffers, enqueued on `stream` (a cudaStream_t;
+ * NULL = legacy default stream); returns after enqueueing.  `status`
+ * (device int32, may be NULL) receives the step's result code.  All input
+ * buffers must stay valid and unchanged until the stream reaches the end
+ * of the step.  Graph capture of the stream is allowed. */
+int mppi_solve_async(mppi_handle h, const float* x_hat, const float* ref, const float* obstacles,
+                     int32_t M, const float* u_nom, uint64_t iter, float* u_out, float* u_cmd,
+                     float* u_next, float* x_next, float* costs, int32_t* status, void* stream);
+
+/* One instance of a batched launch.  Pointers are DEVICE pointers with the
+ * layouts above; outputs may be NULL.  The model and the cost weights and
+ * options (c_*, R, Rd, beta, r_uav, quat_metric, tail_mode, shift_alpha,
+ * delay) come from the handle's parameter set; the fields below are per
+ * instance. */
+typedef struct {
+    const float* x_hat;
+    const float* ref;
+    const float* obstacles;
+    const float* u_nom;
+    float* u_out;
+    float* u_cmd;
+    float* u_next;
+    float* x_next;
+    float* costs;
+    int32_t* status;
+    uint64_t* iter_dev; /* optional device counter: when non-NULL the step
+                           uses *iter_dev and increments it on completion  */
+    uint64_t iter;      /* used when iter_dev is NULL                       */
+    int32_t K, N, M;
+    float dt, lambda;
+    float sigma[4];
+    uint64_t seed;
+    uint32_t stream_id;
+    int32_t reserved;   /* must be 0                                        */
+} mppi_instance;
+
+/* Many independent MPPI steps of uneven (K, N, M) in one persistent launch
+ * on `stream` (the batched form of mppi_solve_async).  `instances` is a
+ * HOST array of n descriptors (copied before return).  The launch shape
+ * (block size, samples per warp) is taken from the handle's tuning table
+ * (mppi_autotune) or a default.  Every instance's result equals what
+ * mppi_solve_async returns for it alone with the same launch shape. */
+int mppi_solve_batch(mppi_handle h, const mppi_instance* instances, int32_t n, void* stream);
+
+/* Same as mppi_solve_batch, replayed from a CUDA graph captured once per
+ * (capacity bucket, launch shape) and cached in the handle; descriptors
+ * are updated in place between replays. */
+int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_t n, void* stream);
+
+/* Launch shape of the rollout kernel. */
+typedef struct {
+    int32_t block;          /* threads per block: 64, 128, 256 or 512       */
+    int32_t lanes;          /* lanes per sample: 1 (one thread per sample),
+                               2, 4 or 8 (warp split of the obstacle loop)  */
+} mppi_shape;
+
+/* Forces a launch shape for subsequent calls on the handle (both 0: back
+ * to the tuned/default choice). */
+int mppi_set_shape(mppi_handle h, const mppi_shape* shape);
+
+/* Project autotuner: times every candidate shape on a synthetic problem of
+ * size (K, N, M) on `stream`, stores the fastest in the handle's table for
+ * that size bucket and returns it in *best (may be NULL).  Synchronous. */
+int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* best, void* stream);
+
+/* Looks up the shape the handle uses for a problem of size (K, N, M). */
+int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* shape);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPPI_GB300_H */

@@ -1,0 +1,731 @@
+// C ABI of the MPPI library: handles, argument validation, workspace
+// management, the single-instance and batched launches, the CUDA-graph
+// cache and the launch-shape autotuner.  See include/mppi.h for the
+// contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "mppi_internal.h"
+
+using namespace mppi;
+
+namespace {
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid = 0;
+};
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
+bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
+
+int check_model(const mppi_model* m) {
+    if (!m) return MPPI_EINVAL;
+    if (!finite_pos(m->mass) || !finite_nonneg(m->g) || !finite_pos(m->arm_l) || !finite_pos(m->c_tf))
+        return MPPI_EINVAL;
+    for (int i = 0; i < 3; ++i)
+        if (!finite_pos(m->J[i]) || !finite_nonneg(m->w_max[i])) return MPPI_EINVAL;
+    if (!std::isfinite(m->T_min) || !std::isfinite(m->T_max) || m->T_min > m->T_max) return MPPI_EINVAL;
+    if (!std::isfinite(m->F_min) || !std::isfinite(m->F_max) || m->F_min > m->F_max) return MPPI_EINVAL;
+    if (m->motor_clip != 0 && m->motor_clip != 1) return MPPI_EINVAL;
+    return MPPI_OK;
+}
+
+int check_step(int K, int N, float dt, float lambda, const float* sigma) {
+    if (K < 1 || K > MPPI_K_MAX || N < 1 || N > MPPI_N_MAX) return MPPI_EINVAL;
+    if (!finite_pos(dt) || !finite_pos(lambda)) return MPPI_EINVAL;
+    for (int c = 0; c < 4; ++c)
+        if (!finite_nonneg(sigma[c])) return MPPI_EINVAL;
+    return MPPI_OK;
+}
+
+int check_params(const mppi_params* p) {
+    if (!p) return MPPI_EINVAL;
+    int rc = check_step(p->K, p->N, p->dt, p->lambda, p->sigma);
+    if (rc) return rc;
+    const float w[] = {p->c_p, p->c_q, p->c_v, p->c_w, p->c_obs, p->c_bar, p->beta, p->r_uav, p->delay};
+    for (float v : w)
+        if (!finite_nonneg(v)) return MPPI_EINVAL;
+    for (int c = 0; c < 4; ++c)
+        if (!finite_nonneg(p->R[c]) || !finite_nonneg(p->Rd[c])) return MPPI_EINVAL;
+    if (p->quat_metric != 0 && p->quat_metric != 1) return MPPI_EINVAL;
+    if (p->tail_mode != 0 && p->tail_mode != 1) return MPPI_EINVAL;
+    if (!(p->shift_alpha > 0.0f && p->shift_alpha <= 1.0f)) return MPPI_EINVAL;
+    if (p->reserved != 0) return MPPI_EINVAL;
+    return MPPI_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+
+DevModel make_dev_model(const mppi_model& m) {
+    DevModel d;
+    std::memset(&d, 0, sizeof(d));
+    const double J[3] = {m.J[0], m.J[1], m.J[2]};
+    d.inv_mass = (float)(1.0 / m.mass);
+    d.g = m.g;
+    d.Jx = m.J[0]; d.Jy = m.J[1]; d.Jz = m.J[2];
+    d.inv_Jx = (float)(1.0 / J[0]); d.inv_Jy = (float)(1.0 / J[1]); d.inv_Jz = (float)(1.0 / J[2]);
+    d.dJx = (float)(J[2] - J[1]); d.dJy = (float)(J[0] - J[2]); d.dJz = (float)(J[1] - J[0]);
+    d.kx = (float)((J[2] - J[1]) / J[0]); d.ky = (float)((J[0] - J[2]) / J[1]); d.kz = (float)((J[1] - J[0]) / J[2]);
+    const double a = (double)m.arm_l / std::sqrt(2.0), c = m.c_tf;
+    d.a = (float)a;
+    d.c_tf = m.c_tf;
+    // The allocation matrix of Sec. III-B has mutually orthogonal rows, so
+    // Gamma^-1 = Gamma^T diag(1/|row_i|^2).
+    const double G[4][4] = {{1, 1, 1, 1}, {-a, a, a, -a}, {-a, a, -a, a}, {-c, -c, c, c}};
+    const double n2[4] = {4.0, 4.0 * a * a, 4.0 * a * a, 4.0 * c * c};
+    for (int r = 0; r < 4; ++r)
+        for (int col = 0; col < 4; ++col) d.Ginv[4 * r + col] = (float)(G[col][r] / n2[col]);
+    d.T_min = m.T_min; d.T_max = m.T_max; d.motor_clip = m.motor_clip;
+    d.F_min = m.F_min; d.F_max = m.F_max;
+    for (int i = 0; i < 3; ++i) d.w_max[i] = m.w_max[i];
+    d.u_init[0] = (float)((double)m.mass * m.g);
+    return d;
+}
+
+DevCost make_dev_cost(const mppi_params& p) {
+    DevCost c;
+    std::memset(&c, 0, sizeof(c));
+    c.c_p = p.c_p; c.c_q = p.c_q; c.c_v = p.c_v; c.c_w = p.c_w;
+    for (int i = 0; i < 4; ++i) { c.R[i] = p.R[i]; c.Rd[i] = p.Rd[i]; }
+    c.c_obs = p.c_obs; c.c_bar = p.c_bar;
+    c.beta_log2e = (float)((double)p.beta * 1.4426950408889634073599);
+    c.r_uav = p.r_uav;
+    c.quat_metric = p.quat_metric; c.tail_mode = p.tail_mode;
+    c.shift_alpha = p.shift_alpha; c.delay = p.delay;
+    return c;
+}
+
+int ceil_log2(long long v) {
+    int r = 0;
+    while ((1ll << r) < v) ++r;
+    return r;
+}
+
+uint64_t bucket_key(long long K, int N, int M) {
+    return ((uint64_t)ceil_log2(K) << 16) | ((uint64_t)ceil_log2(N) << 8) | (uint64_t)(M > 0 ? ceil_log2(M) + 1 : 0);
+}
+
+Shape default_shape(long long K, int N, int M) {
+    (void)N;
+    // Few samples and many obstacles: split the obstacle loop across lanes
+    // so that more warps cover the serial horizon; otherwise one thread
+    // per sample.
+    if (M >= 64 && K <= 8192) return Shape{128, 4};
+    if (M >= 32 && K <= 32768) return Shape{128, 2};
+    return Shape{128, 1};
+}
+
+int bucket_pow2(int v, int lo) {
+    int b = lo;
+    while (b < v) b <<= 1;
+    return b;
+}
+
+}  // namespace
+
+struct mppi_ctx {
+    int device = 0;
+    mppi_model model{};
+    mppi_params params{};
+    mppi_capacity cap{};
+    DevModel dm{};
+    DevCost dc{};
+
+    float* partials = nullptr;
+    size_t partial_floats = 0;
+    unsigned* counters = nullptr;  // [0] tile counter, [1..cap] done, [cap+1..2cap] errflags
+    int counter_inst = 0;
+    int* d_ntiles = nullptr;
+    DevInstance* d_insts = nullptr;
+    int2* d_tilemap = nullptr;
+    size_t inst_cap = 0, tile_cap = 0;
+    DevInstance* h_insts = nullptr;
+    int2* h_tilemap = nullptr;
+    int* h_ntiles = nullptr;
+    cudaEvent_t ev_staging = nullptr;
+
+    float* d_io = nullptr;
+    float* h_io = nullptr;
+    size_t io_floats = 0;
+    cudaStream_t stream = nullptr;
+
+    Shape forced{0, 0};
+    std::map<uint64_t, Shape> table;
+    std::map<uint64_t, GraphEntry> graphs;
+    cudaStream_t capture_stream = nullptr;
+};
+
+namespace {
+
+void drop_graphs(mppi_ctx* h) {
+    for (auto& kv : h->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    h->graphs.clear();
+}
+
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// Grows a device buffer; refuses while the stream is being captured.
+template <typename T>
+int ensure_dev(T** p, size_t* cap, size_t need, cudaStream_t s, mppi_ctx* h) {
+    if (need <= *cap && *p) return MPPI_OK;
+    if (stream_capturing(s)) return MPPI_ENOMEM;
+    cudaStreamSynchronize(s);
+    cudaStreamSynchronize(h->stream);
+    size_t n = std::max(need, *cap * 2);
+    T* q = nullptr;
+    if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return MPPI_ENOMEM;
+    }
+    if (*p) cudaFree(*p);
+    *p = q;
+    *cap = n;
+    drop_graphs(h);
+    return MPPI_OK;
+}
+
+int ensure_counters(mppi_ctx* h, int n_inst, cudaStream_t s) {
+    if (n_inst <= h->counter_inst && h->counters) return MPPI_OK;
+    if (stream_capturing(s)) return MPPI_ENOMEM;
+    cudaStreamSynchronize(s);
+    cudaStreamSynchronize(h->stream);
+    int n = std::max(n_inst, 2 * h->counter_inst);
+    unsigned* q = nullptr;
+    if (cudaMalloc(&q, sizeof(unsigned) * (1 + 2 * (size_t)n)) != cudaSuccess) {
+        cudaGetLastError();
+        return MPPI_ENOMEM;
+    }
+    if (cudaMemset(q, 0, sizeof(unsigned) * (1 + 2 * (size_t)n)) != cudaSuccess) {
+        cudaFree(q);
+        return MPPI_ECUDA;
+    }
+    if (h->counters) cudaFree(h->counters);
+    h->counters = q;
+    h->counter_inst = n;
+    drop_graphs(h);
+    return MPPI_OK;
+}
+
+int ensure_host_staging(mppi_ctx* h, size_t n_inst, size_t n_tiles) {
+    if (h->ev_staging) cudaEventSynchronize(h->ev_staging);
+    if (n_inst > h->inst_cap || !h->h_insts) {
+        size_t n = std::max(n_inst, 2 * h->inst_cap);
+        if (h->h_insts) cudaFreeHost(h->h_insts);
+        h->h_insts = nullptr;
+        if (cudaMallocHost(&h->h_insts, n * sizeof(DevInstance)) != cudaSuccess) return MPPI_ENOMEM;
+        DevInstance* d = nullptr;
+        if (cudaMalloc(&d, n * sizeof(DevInstance)) != cudaSuccess) return MPPI_ENOMEM;
+        if (h->d_insts) cudaFree(h->d_insts);
+        h->d_insts = d;
+        h->inst_cap = n;
+        drop_graphs(h);
+    }
+    if (n_tiles > h->tile_cap || !h->h_tilemap) {
+        size_t n = std::max(n_tiles, 2 * h->tile_cap);
+        if (h->h_tilemap) cudaFreeHost(h->h_tilemap);
+        h->h_tilemap = nullptr;
+        if (cudaMallocHost(&h->h_tilemap, n * sizeof(int2)) != cudaSuccess) return MPPI_ENOMEM;
+        int2* d = nullptr;
+        if (cudaMalloc(&d, n * sizeof(int2)) != cudaSuccess) return MPPI_ENOMEM;
+        if (h->d_tilemap) cudaFree(h->d_tilemap);
+        h->d_tilemap = d;
+        h->tile_cap = n;
+        drop_graphs(h);
+    }
+    return MPPI_OK;
+}
+
+DevInstance make_instance(const mppi_ctx* h, const mppi_instance& in, Shape s) {
+    DevInstance d;
+    std::memset(&d, 0, sizeof(d));
+    d.x_hat = in.x_hat; d.ref = in.ref; d.obs = reinterpret_cast<const float4*>(in.obstacles);
+    d.u_nom = in.u_nom; d.u_out = in.u_out; d.u_cmd = in.u_cmd; d.u_next = in.u_next;
+    d.x_next = in.x_next; d.costs = in.costs; d.status = in.status;
+    d.iter_dev = reinterpret_cast<unsigned long long*>(in.iter_dev);
+    d.iter = in.iter;
+    d.K = in.K; d.N = in.N; d.M = in.M;
+    d.n_tiles = (in.K + s.block / s.lanes - 1) / (s.block / s.lanes);
+    d.dt = in.dt; d.lambda = in.lambda;
+    for (int c = 0; c < 4; ++c) d.sigma[c] = in.sigma[c];
+    d.key0 = (unsigned)(in.seed & 0xffffffffu);
+    d.key1 = (unsigned)(in.seed >> 32) ^ in.stream_id;
+    (void)h;
+    return d;
+}
+
+int check_instance(const mppi_instance& in, const mppi_ctx* h) {
+    int rc = check_step(in.K, in.N, in.dt, in.lambda, in.sigma);
+    if (rc) return rc;
+    if (in.M < 0 || in.M > MPPI_M_MAX || in.reserved != 0) return MPPI_EINVAL;
+    if (!in.x_hat || !in.ref || !in.u_nom) return MPPI_EINVAL;
+    if (in.M > 0 && (!in.obstacles || !aligned16(in.obstacles))) return MPPI_EINVAL;
+    const void* ptrs[] = {in.x_hat, in.ref, in.u_nom, in.u_out, in.u_cmd, in.u_next, in.x_next, in.costs, in.status};
+    for (const void* p : ptrs)
+        if (p && !aligned4(p)) return MPPI_EINVAL;
+    if (in.iter_dev && (reinterpret_cast<uintptr_t>(in.iter_dev) & 7u)) return MPPI_EINVAL;
+    (void)h;
+    return MPPI_OK;
+}
+
+Shape choose_shape(const mppi_ctx* h, long long K, int N, int M) {
+    if (h->forced.block) return h->forced;
+    auto it = h->table.find(bucket_key(K, N, M));
+    if (it != h->table.end()) return it->second;
+    return default_shape(K, N, M);
+}
+
+LaunchArgs base_args(mppi_ctx* h, int n_inst) {
+    LaunchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.partials = h->partials;
+    a.done = h->counters + 1;
+    a.errflags = h->counters + 1 + n_inst;
+    a.M = h->dm;
+    a.C = h->dc;
+    return a;
+}
+
+// Single instance, one tile per block, no descriptor upload.
+int launch_single(mppi_ctx* h, const mppi_instance& in, Shape s, cudaStream_t st) {
+    DevInstance d = make_instance(h, in, s);
+    d.part_off = 0;
+    const size_t need = (size_t)d.n_tiles * partial_stride(in.N);
+    int rc = ensure_dev(&h->partials, &h->partial_floats, need, st, h);
+    if (rc) return rc;
+    if ((rc = ensure_counters(h, std::max(1, h->cap.max_instances), st))) return rc;
+    LaunchArgs a = base_args(h, h->counter_inst);
+    a.single = d;
+    a.n_tiles = d.n_tiles;
+    a.n_inst = 1;
+    a.N_max = in.N;
+    a.M_max = in.M;
+    const size_t smem = smem_bytes(in.N, in.M, s);
+    if (smem > 227 * 1024) return MPPI_EINVAL;
+    cudaError_t e = launch_tiles(a, s, d.n_tiles, smem, st);
+    return e == cudaSuccess ? MPPI_OK : MPPI_ECUDA;
+}
+
+struct BatchPlan {
+    int n_tiles = 0;
+    int N_b = 0, M_b = 0;
+    size_t partial_floats = 0;
+    Shape s{0, 0};
+};
+
+// Fills the pinned descriptor and tile-map staging for a batched launch:
+// tiles ordered longest-first (estimated cost N (1 + M / 8)).
+int plan_batch(mppi_ctx* h, const mppi_instance* ins, int n, BatchPlan* plan) {
+    long long sumK = 0;
+    int Nmax = 1, Mmax = 0;
+    for (int i = 0; i < n; ++i) {
+        int rc = check_instance(ins[i], h);
+        if (rc) return rc;
+        sumK += ins[i].K;
+        Nmax = std::max(Nmax, ins[i].N);
+        Mmax = std::max(Mmax, ins[i].M);
+    }
+    Shape s = choose_shape(h, sumK / n, Nmax, Mmax);
+    const int spb = s.block / s.lanes;
+    long long tiles = 0;
+    size_t pf = 0;
+    for (int i = 0; i < n; ++i) {
+        const int t = (ins[i].K + spb - 1) / spb;
+        tiles += t;
+        pf += (size_t)t * partial_stride(ins[i].N);
+    }
+    if (tiles > (1ll << 30)) return MPPI_EINVAL;
+    int rc = ensure_host_staging(h, (size_t)n, (size_t)tiles);
+    if (rc) return rc;
+    if (!h->h_ntiles && cudaMallocHost(&h->h_ntiles, sizeof(int)) != cudaSuccess) return MPPI_ENOMEM;
+    size_t off = 0;
+    std::vector<std::pair<float, int2>> order;
+    order.reserve((size_t)tiles);
+    for (int i = 0; i < n; ++i) {
+        DevInstance d = make_instance(h, ins[i], s);
+        d.part_off = (long long)off;
+        off += (size_t)d.n_tiles * partial_stride(ins[i].N);
+        h->h_insts[i] = d;
+        const float w = (float)ins[i].N * (1.0f + ins[i].M / 8.0f);
+        for (int t = 0; t < d.n_tiles; ++t) order.push_back({w, make_int2(i, t)});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<float, int2>& x, const std::pair<float, int2>& y) { return x.first > y.first; });
+    for (size_t t = 0; t < order.size(); ++t) h->h_tilemap[t] = order[t].second;
+    *h->h_ntiles = (int)tiles;
+    plan->n_tiles = (int)tiles;
+    plan->N_b = bucket_pow2(Nmax, 16);
+    plan->M_b = Mmax > 0 ? bucket_pow2(Mmax, 16) : 0;
+    plan->partial_floats = off;
+    plan->s = s;
+    return MPPI_OK;
+}
+
+int upload_batch(mppi_ctx* h, int n, const BatchPlan& plan, cudaStream_t st) {
+    int rc = ensure_dev(&h->partials, &h->partial_floats, plan.partial_floats, st, h);
+    if (rc) return rc;
+    if ((rc = ensure_counters(h, std::max(n, h->cap.max_instances), st))) return rc;
+    if (!h->d_ntiles) {
+        if (stream_capturing(st)) return MPPI_ENOMEM;
+        if (cudaMalloc(&h->d_ntiles, sizeof(int)) != cudaSuccess) return MPPI_ENOMEM;
+    }
+    if (cudaMemcpyAsync(h->d_insts, h->h_insts, sizeof(DevInstance) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(h->d_tilemap, h->h_tilemap, sizeof(int2) * plan.n_tiles, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(h->d_ntiles, h->h_ntiles, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return MPPI_ECUDA;
+    if (cudaEventRecord(h->ev_staging, st) != cudaSuccess) return MPPI_ECUDA;
+    return MPPI_OK;
+}
+
+LaunchArgs batch_args(mppi_ctx* h, const BatchPlan& plan) {
+    LaunchArgs a = base_args(h, h->counter_inst);
+    a.insts = h->d_insts;
+    a.tile_map = h->d_tilemap;
+    a.tile_counter = h->counters;
+    a.n_tiles_dev = h->d_ntiles;
+    a.n_tiles = plan.n_tiles;
+    a.N_max = plan.N_b;
+    a.M_max = plan.M_b;
+    return a;
+}
+
+int persistent_grid(Shape s, size_t smem) { return sm_count() * max_active_blocks(s, smem); }
+
+}  // namespace
+
+extern "C" {
+
+const char* mppi_version(void) { return "gb300-mppi 1.0 (sm_103a)"; }
+
+const char* mppi_strerror(int code) {
+    switch (code) {
+        case MPPI_OK: return "ok";
+        case MPPI_EINVAL: return "invalid argument";
+        case MPPI_ENOMEM: return "out of device memory or admission budget";
+        case MPPI_ECUDA: return "CUDA runtime error";
+        case MPPI_ETIMEOUT: return "bounded device wait timed out";
+        case MPPI_ENONFINITE: return "every rollout cost was non-finite";
+        case MPPI_EAGAIN: return "queue full or nothing ready";
+        case MPPI_ENOTFOUND: return "unknown vehicle or request";
+        default: return "unknown error";
+    }
+}
+
+int mppi_create(const mppi_model* model, const mppi_params* params, const mppi_capacity* cap, mppi_handle* out) {
+    if (!out) return MPPI_EINVAL;
+    *out = nullptr;
+    int rc = check_model(model);
+    if (rc) return rc;
+    if ((rc = check_params(params))) return rc;
+    mppi_capacity c;
+    if (cap) {
+        c = *cap;
+        if (c.max_instances < 1 || c.max_samples < 1 || c.N_max < 1 || c.N_max > MPPI_N_MAX || c.M_max < 0 ||
+            c.M_max > MPPI_M_MAX)
+            return MPPI_EINVAL;
+    } else {
+        c.max_instances = 1;
+        c.max_samples = params->K;
+        c.N_max = params->N;
+        c.M_max = MPPI_M_MAX;
+    }
+    if (params->K > c.max_samples || params->N > c.N_max) return MPPI_EINVAL;
+
+    mppi_ctx* h = new (std::nothrow) mppi_ctx();
+    if (!h) return MPPI_ENOMEM;
+    cudaGetDevice(&h->device);
+    h->model = *model;
+    h->params = *params;
+    h->cap = c;
+    h->dm = make_dev_model(*model);
+    h->dc = make_dev_cost(*params);
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_staging, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        mppi_destroy(h);
+        return MPPI_ECUDA;
+    }
+    // Workspace for the default launch shape at full capacity.
+    const long long tiles = (c.max_samples + 127) / 128 + c.max_instances;
+    rc = ensure_dev(&h->partials, &h->partial_floats, (size_t)tiles * partial_stride(c.N_max), h->stream, h);
+    if (!rc) rc = ensure_counters(h, c.max_instances, h->stream);
+    if (rc) {
+        mppi_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return MPPI_OK;
+}
+
+void mppi_destroy(mppi_handle h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    cudaFree(h->partials);
+    cudaFree(h->counters);
+    cudaFree(h->d_ntiles);
+    cudaFree(h->d_insts);
+    cudaFree(h->d_tilemap);
+    cudaFree(h->d_io);
+    if (h->h_insts) cudaFreeHost(h->h_insts);
+    if (h->h_tilemap) cudaFreeHost(h->h_tilemap);
+    if (h->h_ntiles) cudaFreeHost(h->h_ntiles);
+    if (h->h_io) cudaFreeHost(h->h_io);
+    if (h->ev_staging) cudaEventDestroy(h->ev_staging);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    delete h;
+}
+
+int mppi_set_params(mppi_handle h, const mppi_params* params) {
+    if (!h) return MPPI_EINVAL;
+    int rc = check_params(params);
+    if (rc) return rc;
+    h->params = *params;
+    h->dc = make_dev_cost(*params);
+    drop_graphs(h);
+    return MPPI_OK;
+}
+
+int mppi_set_shape(mppi_handle h, const mppi_shape* shape) {
+    if (!h || !shape) return MPPI_EINVAL;
+    if (shape->block == 0 && shape->lanes == 0) {
+        h->forced = Shape{0, 0};
+        return MPPI_OK;
+    }
+    Shape s{shape->block, shape->lanes};
+    if (!shape_supported(s)) return MPPI_EINVAL;
+    h->forced = s;
+    return MPPI_OK;
+}
+
+int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* shape) {
+    if (!h || !shape || K < 1 || N < 1 || M < 0) return MPPI_EINVAL;
+    Shape s = choose_shape(h, K, N, M);
+    shape->block = s.block;
+    shape->lanes = s.lanes;
+    return MPPI_OK;
+}
+
+static mppi_instance instance_from_params(const mppi_params& p, const float* x_hat, const float* ref,
+                                          const float* obstacles, int32_t M, const float* u_nom, uint64_t iter,
+                                          float* u_out, float* u_cmd, float* u_next, float* x_next, float* costs,
+                                          int32_t* status) {
+    mppi_instance in;
+    std::memset(&in, 0, sizeof(in));
+    in.x_hat = x_hat; in.ref = ref; in.obstacles = obstacles; in.u_nom = u_nom;
+    in.u_out = u_out; in.u_cmd = u_cmd; in.u_next = u_next; in.x_next = x_next; in.costs = costs;
+    in.status = status; in.iter = iter;
+    in.K = p.K; in.N = p.N; in.M = M;
+    in.dt = p.dt; in.lambda = p.lambda;
+    for (int c = 0; c < 4; ++c) in.sigma[c] = p.sigma[c];
+    in.seed = p.seed;
+    in.stream_id = p.stream_id;
+    return in;
+}
+
+int mppi_solve_async(mppi_handle h, const float* x_hat, const float* ref, const float* obstacles, int32_t M,
+                     const float* u_nom, uint64_t iter, float* u_out, float* u_cmd, float* u_next, float* x_next,
+                     float* costs, int32_t* status, void* stream) {
+    if (!h) return MPPI_EINVAL;
+    mppi_instance in = instance_from_params(h->params, x_hat, ref, obstacles, M, u_nom, iter, u_out, u_cmd, u_next,
+                                            x_next, costs, status);
+    int rc = check_instance(in, h);
+    if (rc) return rc;
+    Shape s = choose_shape(h, in.K, in.N, in.M);
+    return launch_single(h, in, s, (cudaStream_t)stream);
+}
+
+// Host-buffer solve: inputs packed into one pinned block and one device
+// block, one copy each way.
+int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float* obstacles, int32_t M,
+               const float* u_nom, uint64_t iter, float* u_out, float* u_cmd, float* u_next, float* x_next,
+               float* costs) {
+    if (!h || !x_hat || !ref || !u_nom) return MPPI_EINVAL;
+    if (M < 0 || M > MPPI_M_MAX || (M > 0 && !obstacles)) return MPPI_EINVAL;
+    const int K = h->params.K, N = h->params.N;
+    // Layout in floats (16-byte aligned segments).
+    auto up4 = [](size_t v) { return (v + 3) / 4 * 4; };
+    const size_t o_x = 0, o_ref = 16, o_obs = up4(o_ref + 13 * (size_t)(N + 1)), o_u = up4(o_obs + 4 * (size_t)M);
+    const size_t in_end = up4(o_u + 4 * (size_t)N);
+    const size_t o_uo = in_end, o_uc = up4(o_uo + 4 * (size_t)N), o_un = o_uc + 4, o_xn = up4(o_un + 4 * (size_t)N),
+                 o_st = o_xn + 16, o_c = o_st + 4;
+    const size_t total = o_c + (costs ? (size_t)K : 0);
+    if (total > h->io_floats || !h->h_io) {
+        if (h->h_io) cudaFreeHost(h->h_io);
+        if (h->d_io) cudaFree(h->d_io);
+        h->h_io = nullptr;
+        h->d_io = nullptr;
+        h->io_floats = 0;
+        if (cudaMallocHost(&h->h_io, total * sizeof(float)) != cudaSuccess) return MPPI_ENOMEM;
+        if (cudaMalloc(&h->d_io, total * sizeof(float)) != cudaSuccess) return MPPI_ENOMEM;
+        h->io_floats = total;
+    }
+    float* hb = h->h_io;
+    std::memcpy(hb + o_x, x_hat, 13 * sizeof(float));
+    std::memcpy(hb + o_ref, ref, 13 * sizeof(float) * (size_t)(N + 1));
+    if (M > 0) std::memcpy(hb + o_obs, obstacles, 4 * sizeof(float) * (size_t)M);
+    std::memcpy(hb + o_u, u_nom, 4 * sizeof(float) * (size_t)N);
+    float* db = h->d_io;
+    cudaStream_t st = h->stream;
+    if (cudaMemcpyAsync(db, hb, in_end * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) return MPPI_ECUDA;
+    int32_t* dstatus = reinterpret_cast<int32_t*>(db + o_st);
+    int rc = mppi_solve_async(h, db + o_x, db + o_ref, M > 0 ? db + o_obs : nullptr, M, db + o_u, iter, db + o_uo,
+                              db + o_uc, db + o_un, db + o_xn, costs ? db + o_c : nullptr, dstatus, st);
+    if (rc) {
+        cudaStreamSynchronize(st);
+        return rc;
+    }
+    if (cudaMemcpyAsync(hb + in_end, db + in_end, (total - in_end) * sizeof(float), cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return MPPI_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MPPI_ECUDA;
+    if (u_out) std::memcpy(u_out, hb + o_uo, 4 * sizeof(float) * (size_t)N);
+    if (u_cmd) std::memcpy(u_cmd, hb + o_uc, 4 * sizeof(float));
+    if (u_next) std::memcpy(u_next, hb + o_un, 4 * sizeof(float) * (size_t)N);
+    if (x_next) std::memcpy(x_next, hb + o_xn, 13 * sizeof(float));
+    if (costs) std::memcpy(costs, hb + o_c, sizeof(float) * (size_t)K);
+    int32_t status;
+    std::memcpy(&status, hb + o_st, sizeof(status));
+    return status;
+}
+
+int mppi_solve_batch(mppi_handle h, const mppi_instance* instances, int32_t n, void* stream) {
+    if (!h || !instances || n < 1) return MPPI_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    BatchPlan plan;
+    int rc = plan_batch(h, instances, n, &plan);
+    if (rc) return rc;
+    if ((rc = upload_batch(h, n, plan, st))) return rc;
+    const size_t smem = smem_bytes(plan.N_b, plan.M_b, plan.s);
+    if (smem > 227 * 1024) return MPPI_EINVAL;
+    if (cudaMemsetAsync(h->counters, 0, sizeof(unsigned), st) != cudaSuccess) return MPPI_ECUDA;
+    LaunchArgs a = batch_args(h, plan);
+    const int grid = std::min(plan.n_tiles, persistent_grid(plan.s, smem));
+    return launch_tiles(a, plan.s, grid, smem, st) == cudaSuccess ? MPPI_OK : MPPI_ECUDA;
+}
+
+int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_t n, void* stream) {
+    if (!h || !instances || n < 1) return MPPI_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    BatchPlan plan;
+    int rc = plan_batch(h, instances, n, &plan);
+    if (rc) return rc;
+    if ((rc = upload_batch(h, n, plan, st))) return rc;
+    const size_t smem = smem_bytes(plan.N_b, plan.M_b, plan.s);
+    if (smem > 227 * 1024) return MPPI_EINVAL;
+    const uint64_t key = ((uint64_t)plan.s.block << 48) | ((uint64_t)plan.s.lanes << 40) |
+                         ((uint64_t)plan.N_b << 20) | (uint64_t)plan.M_b;
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        GraphEntry g;
+        g.grid = persistent_grid(plan.s, smem);
+        LaunchArgs a = batch_args(h, plan);
+        cudaStream_t cs = h->capture_stream;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MPPI_ECUDA;
+        cudaMemsetAsync(h->counters, 0, sizeof(unsigned), cs);
+        launch_tiles(a, plan.s, g.grid, smem, cs);
+        if (cudaStreamEndCapture(cs, &g.graph) != cudaSuccess) {
+            cudaGetLastError();
+            return MPPI_ECUDA;
+        }
+        if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(g.graph);
+            cudaGetLastError();
+            return MPPI_ECUDA;
+        }
+        it = h->graphs.emplace(key, g).first;
+    }
+    return cudaGraphLaunch(it->second.exec, st) == cudaSuccess ? MPPI_OK : MPPI_ECUDA;
+}
+
+int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* best, void* stream) {
+    if (!h || K < 1 || K > MPPI_K_MAX || N < 1 || N > MPPI_N_MAX || M < 0 || M > MPPI_M_MAX) return MPPI_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // Synthetic problem: hover reference, start 0.5 m off, M spheres on a
+    // ring 3..8 m away (finite, non-trivial obstacle cost).
+    std::vector<float> xh(13, 0.0f), ref(13 * (size_t)(N + 1), 0.0f), u(4 * (size_t)N, 0.0f), obs(4 * (size_t)M);
+    xh[0] = 0.5f; xh[3] = 1.0f;
+    for (int j = 0; j <= N; ++j) ref[13 * (size_t)j + 3] = 1.0f;
+    for (int j = 0; j < N; ++j) u[4 * (size_t)j] = h->dm.u_init[0];
+    for (int o = 0; o < M; ++o) {
+        const float ang = 2.399963f * o, rad = 3.0f + 5.0f * (o % 7) / 7.0f;
+        obs[4 * o + 0] = rad * cosf(ang); obs[4 * o + 1] = rad * sinf(ang);
+        obs[4 * o + 2] = 0.5f * (o % 5); obs[4 * o + 3] = (o % 3 == 2) ? -0.5f : 0.6f;
+    }
+    float* d = nullptr;
+    const size_t o_ref = 16, o_u = o_ref + ref.size() + 4, o_obs = (o_u + u.size() + 3) / 4 * 4 + 4,
+                 o_out = o_obs + obs.size() + 4;
+    const size_t total = o_out + 4 * (size_t)N + 64;
+    if (cudaMalloc(&d, total * sizeof(float)) != cudaSuccess) return MPPI_ENOMEM;
+    cudaMemcpy(d, xh.data(), 13 * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(d + o_ref, ref.data(), ref.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(d + o_u, u.data(), u.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (M) cudaMemcpy(d + o_obs, obs.data(), obs.size() * sizeof(float), cudaMemcpyHostToDevice);
+    mppi_params p = h->params;
+    p.K = K;
+    p.N = N;
+    mppi_instance in = instance_from_params(p, d, d + o_ref, M ? d + o_obs : nullptr, M, d + o_u, 0, d + o_out,
+                                            nullptr, nullptr, nullptr, nullptr, nullptr);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks[] = {64, 128, 256, 512};
+    const int lanes[] = {1, 2, 4, 8};
+    Shape bestS{128, 1};
+    float bestT = 1e30f;
+    int rc = MPPI_OK;
+    for (int b : blocks) {
+        for (int l : lanes) {
+            Shape s{b, l};
+            if (b / l < 8) continue;
+            if (smem_bytes(N, M, s) > 227 * 1024) continue;
+            if ((rc = launch_single(h, in, s, st))) break;  // warm-up
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3; ++r) launch_single(h, in, s, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = MPPI_ECUDA;
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < bestT) {
+                bestT = ms;
+                bestS = s;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (rc) return rc;
+    h->table[bucket_key(K, N, M)] = bestS;
+    if (best) {
+        best->block = bestS.block;
+        best->lanes = bestS.lanes;
+    }
+    return MPPI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Internal declarations shared by the CUDA kernels, the C ABI and the
+// serving runtime.  Nothing here is part of the public ABI (include/mppi.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mppi.h"
+
+#ifdef __CUDACC__
+#define MPPI_HD __host__ __device__
+#else
+#define MPPI_HD
+#endif
+
+namespace mppi {
+
+// Vehicle model in the form the kernels use (derived on the host, FP64,
+// then rounded once to FP32).
+struct DevModel {
+    float inv_mass, g;
+    float Jx, Jy, Jz;
+    float inv_Jx, inv_Jy, inv_Jz;
+    float dJx, dJy, dJz;    // (Jz-Jy), (Jx-Jz), (Jy-Jx): omega x J omega terms
+    float kx, ky, kz;       // dJ / J: gyroscopic angular-acceleration factors
+    float a, c_tf;          // a = l / sqrt(2): entries of the allocation matrix
+    float Ginv[16];         // inverse allocation matrix, row major
+    float T_min, T_max;
+    int motor_clip;
+    float F_min, F_max;
+    float w_max[3];
+    float u_init[4];        // hover: m g, 0, 0, 0
+};
+
+// Cost weights and step options shared by every instance of a launch.
+struct DevCost {
+    float c_p, c_q, c_v, c_w;
+    float R[4], Rd[4];
+    float c_obs, c_bar, beta_log2e, r_uav;
+    int quat_metric, tail_mode;
+    float shift_alpha, delay;
+};
+
+// One instance (vehicle problem) of a launch.
+struct DevInstance {
+    const float* x_hat;
+    const float* ref;
+    const float4* obs;
+    const float* u_nom;
+    float* u_out;
+    float* u_cmd;
+    float* u_next;
+    float* x_next;
+    float* costs;
+    int* status;
+    unsigned long long* iter_dev;
+    unsigned long long iter;
+    long long part_off;     // float offset of this instance's first tile partial
+    int K, N, M, n_tiles;
+    float dt, lambda;
+    float sigma[4];
+    unsigned key0, key1;
+};
+
+struct Shape {
+    int block;  // threads per block
+    int lanes;  // lanes per sample
+};
+
+// Everything one launch of the fused kernel needs.
+struct LaunchArgs {
+    const DevInstance* insts;   // device array; NULL: the single instance below
+    const int2* tile_map;       // (instance, tile) per global tile; NULL: (0, t)
+    unsigned* tile_counter;     // dynamic tile scheduler; NULL: one tile per block
+    float* partials;            // per-tile (rho_t, eta_t, s_t, Sigma_t)
+    unsigned* done;             // per-instance count of finished tiles
+    unsigned* errflags;         // per-instance error bits
+    const int* n_tiles_dev;     // device tile count (graph replay); NULL: n_tiles
+    int n_tiles;
+    int n_inst;
+    int N_max, M_max;           // sizes the dynamic shared memory was laid out for
+    DevModel M;
+    DevCost C;
+    DevInstance single;
+};
+
+constexpr unsigned ERR_TIMEOUT = 1u;
+
+// Floats of one tile partial: rho_t (FP64, two slots), eta_t, the merge scale
+// s_t, then Sigma_t[N][4].
+MPPI_HD inline int partial_stride(int N) { return 4 + 4 * N; }
+
+size_t smem_bytes(int N_max, int M_max, Shape s);
+bool shape_supported(Shape s);
+cudaError_t launch_tiles(const LaunchArgs& a, Shape s, int grid, size_t smem, cudaStream_t st);
+int max_active_blocks(Shape s, size_t smem);
+int sm_count();
+
+}  // namespace mppi

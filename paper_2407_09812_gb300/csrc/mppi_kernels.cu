@@ -1,0 +1,777 @@
+// Fused MPPI step kernel for sm_103a.
+//
+// One launch computes, for one or many independent instances (vehicles),
+// the whole MPPI iteration of Alg. 1:
+//   * noise delta u_j^k ~ N(0, Sigma) from a counter-based Philox4x32-10
+//     generator inside the kernel (Sec. III-A, Eq. rollout_computation),
+//     regenerated rather than stored;
+//   * the rollout x_{j+1} = x_j + f_RK4(x_j, u_j, dt) of Eq. drone_dynamics
+//     with the motor-constraint pipeline of Sec. III-B, state in registers;
+//   * the tracking / input / input-change cost of Sec. IV-C and the
+//     obstacle cost of Sec. IV-D fused into the rollout, obstacles staged
+//     in shared memory by a bulk TMA copy;
+//   * per tile of samples: warp-shuffle min, min-shifted exponential
+//     weights (Eq. cost_2) and the weighted sum of the regenerated noise;
+//   * the last block of an instance merges the tile partials in a fixed
+//     order (log-sum-exp rescaling), applies Eq. u_update, computes the
+//     command sent to the low-level controller and the warm-start shift.
+//
+// Tiles are (instance, block of samples).  A persistent grid pulls tiles
+// from an atomic counter (batched launches) or each block takes one tile
+// (single instance).  The per-instance result depends only on the
+// instance and the launch shape, never on what else is in the launch.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "mppi_internal.h"
+
+namespace mppi {
+
+// ------------------------------------------------------------------ noise
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the multiply/xor
+// network, the key bumped by the Weyl constants after each round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const unsigned lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Uniform in (0, 1) from the top 23 bits: (2m + 1) 2^-24, exact in FP32.
+__device__ __forceinline__ float uniform01(unsigned r) {
+    return __uint2float_rn(((r >> 9) << 1) | 1u) * 5.9604644775390625e-08f;
+}
+
+// Four standard normals for sample k, step j: Box-Muller on the two
+// uniform pairs of one Philox call.  Counter (k, j, iter), key (key0, key1).
+__device__ __forceinline__ float4 normals4(unsigned k, unsigned j, unsigned long long iter, unsigned key0,
+                                           unsigned key1) {
+    const uint4 r = philox4x32_10(make_uint4(k, j, (unsigned)iter, (unsigned)(iter >> 32)), key0, key1);
+    const float u0 = uniform01(r.x), u1 = uniform01(r.y), u2 = uniform01(r.z), u3 = uniform01(r.w);
+    const float rad01 = sqrtf(-2.0f * logf(u0));
+    const float rad23 = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    return make_float4(rad01 * c1, rad01 * s1, rad23 * c3, rad23 * s3);
+}
+
+// delta = sigma o z, rounded once (no contraction) so that the rollout and
+// the regeneration in the weighted sum see the same value.
+__device__ __forceinline__ float4 noise_delta(const float4 z, const float* sigma) {
+    return make_float4(__fmul_rn(sigma[0], z.x), __fmul_rn(sigma[1], z.y), __fmul_rn(sigma[2], z.z),
+                       __fmul_rn(sigma[3], z.w));
+}
+
+// ------------------------------------------------------------------ model
+
+struct State {
+    float px, py, pz, qw, qx, qy, qz, vx, vy, vz, wx, wy, wz;
+};
+
+// Eq. drone_dynamics with collective thrust over mass Fm and torque over
+// inertia (tJx, tJy, tJz) held constant over the step.
+__device__ __forceinline__ void deriv(const DevModel& M, const State& s, float Fm, float tJx, float tJy, float tJz,
+                                      State& d) {
+    d.px = s.vx;
+    d.py = s.vy;
+    d.pz = s.vz;
+    const float hx = 0.5f * s.wx, hy = 0.5f * s.wy, hz = 0.5f * s.wz;
+    d.qw = -s.qx * hx - s.qy * hy - s.qz * hz;
+    d.qx = s.qw * hx + s.qy * hz - s.qz * hy;
+    d.qy = s.qw * hy - s.qx * hz + s.qz * hx;
+    d.qz = s.qw * hz + s.qx * hy - s.qy * hx;
+    d.vx = 2.0f * (s.qx * s.qz + s.qw * s.qy) * Fm;
+    d.vy = 2.0f * (s.qy * s.qz - s.qw * s.qx) * Fm;
+    d.vz = (1.0f - 2.0f * (s.qx * s.qx + s.qy * s.qy)) * Fm - M.g;
+    d.wx = tJx - M.kx * s.wy * s.wz;
+    d.wy = tJy - M.ky * s.wz * s.wx;
+    d.wz = tJz - M.kz * s.wx * s.wy;
+}
+
+__device__ __forceinline__ void axpy(State& o, const State& x, float h, const State& k) {
+    o.px = fmaf(h, k.px, x.px); o.py = fmaf(h, k.py, x.py); o.pz = fmaf(h, k.pz, x.pz);
+    o.qw = fmaf(h, k.qw, x.qw); o.qx = fmaf(h, k.qx, x.qx); o.qy = fmaf(h, k.qy, x.qy);
+    o.qz = fmaf(h, k.qz, x.qz);
+    o.vx = fmaf(h, k.vx, x.vx); o.vy = fmaf(h, k.vy, x.vy); o.vz = fmaf(h, k.vz, x.vz);
+    o.wx = fmaf(h, k.wx, x.wx); o.wy = fmaf(h, k.wy, x.wy); o.wz = fmaf(h, k.wz, x.wz);
+}
+
+// Low-order parts of position and velocity (compensated summation).
+struct Comp {
+    float px, py, pz, vx, vy, vz;
+};
+
+__device__ __forceinline__ void comp_add(float& x, float& c, float inc) {
+    const float y = inc - c;
+    const float t = x + y;
+    c = (t - x) - y;
+    x = t;
+}
+
+__device__ __forceinline__ void axpy_inc(State& o, float h, const State& k) {
+    o.px = fmaf(h, k.px, o.px); o.py = fmaf(h, k.py, o.py); o.pz = fmaf(h, k.pz, o.pz);
+    o.qw = fmaf(h, k.qw, o.qw); o.qx = fmaf(h, k.qx, o.qx); o.qy = fmaf(h, k.qy, o.qy);
+    o.qz = fmaf(h, k.qz, o.qz);
+    o.vx = fmaf(h, k.vx, o.vx); o.vy = fmaf(h, k.vy, o.vy); o.vz = fmaf(h, k.vz, o.vz);
+    o.wx = fmaf(h, k.wx, o.wx); o.wy = fmaf(h, k.wy, o.wy); o.wz = fmaf(h, k.wz, o.wz);
+}
+
+// Classical RK4 step of length h, inputs held, then q renormalised.  The
+// four stage increments are summed first and added to the state once;
+// position and velocity carry a compensation term across steps so that
+// their FP32 rounding does not accumulate over the horizon.
+__device__ __forceinline__ void rk4(const DevModel& M, State& x, Comp& c, float Fm, float tJx, float tJy, float tJz,
+                                    float h) {
+    const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
+    State k, xs, inc;
+    deriv(M, x, Fm, tJx, tJy, tJz, k);
+    inc.px = h6 * k.px; inc.py = h6 * k.py; inc.pz = h6 * k.pz;
+    inc.qw = h6 * k.qw; inc.qx = h6 * k.qx; inc.qy = h6 * k.qy; inc.qz = h6 * k.qz;
+    inc.vx = h6 * k.vx; inc.vy = h6 * k.vy; inc.vz = h6 * k.vz;
+    inc.wx = h6 * k.wx; inc.wy = h6 * k.wy; inc.wz = h6 * k.wz;
+    axpy(xs, x, h2, k);
+    deriv(M, xs, Fm, tJx, tJy, tJz, k);
+    axpy_inc(inc, h3, k);
+    axpy(xs, x, h2, k);
+    deriv(M, xs, Fm, tJx, tJy, tJz, k);
+    axpy_inc(inc, h3, k);
+    axpy(xs, x, h, k);
+    deriv(M, xs, Fm, tJx, tJy, tJz, k);
+    axpy_inc(inc, h6, k);
+    comp_add(x.px, c.px, inc.px); comp_add(x.py, c.py, inc.py); comp_add(x.pz, c.pz, inc.pz);
+    comp_add(x.vx, c.vx, inc.vx); comp_add(x.vy, c.vy, inc.vy); comp_add(x.vz, c.vz, inc.vz);
+    x.qw += inc.qw; x.qx += inc.qx; x.qy += inc.qy; x.qz += inc.qz;
+    x.wx += inc.wx; x.wy += inc.wy; x.wz += inc.wz;
+    const float n = rsqrtf(x.qw * x.qw + x.qx * x.qx + x.qy * x.qy + x.qz * x.qz);
+    x.qw *= n; x.qx *= n; x.qy *= n; x.qz *= n;
+}
+
+// Uncompensated step (single use: prediction, plant step).
+__device__ __forceinline__ void rk4(const DevModel& M, State& x, float Fm, float tJx, float tJy, float tJz, float h) {
+    Comp c = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    rk4(M, x, c, Fm, tJx, tJy, tJz, h);
+}
+
+__device__ __forceinline__ float4 clamp_input(const DevModel& M, float4 u) {
+    u.x = fminf(fmaxf(u.x, M.F_min), M.F_max);
+    u.y = fminf(fmaxf(u.y, -M.w_max[0]), M.w_max[0]);
+    u.z = fminf(fmaxf(u.z, -M.w_max[1]), M.w_max[1]);
+    u.w = fminf(fmaxf(u.w, -M.w_max[2]), M.w_max[2]);
+    return u;
+}
+
+struct Feasible {
+    float F, tx, ty, tz;    // clipped collective thrust and torques
+    float gx, gy, gz;       // omega x J omega at the step's start
+};
+
+// Constraint pipeline of Sec. III-B: desired rate change over dt ->
+// desired torque -> rotor thrusts (Gamma^-1) -> clip -> Gamma.
+__device__ __forceinline__ Feasible feasible(const DevModel& M, const State& s, float4 u, float inv_dt) {
+    Feasible o;
+    o.gx = M.dJx * s.wy * s.wz;
+    o.gy = M.dJy * s.wz * s.wx;
+    o.gz = M.dJz * s.wx * s.wy;
+    float F = u.x;
+    float tx = fmaf(M.Jx, (u.y - s.wx) * inv_dt, o.gx);
+    float ty = fmaf(M.Jy, (u.z - s.wy) * inv_dt, o.gy);
+    float tz = fmaf(M.Jz, (u.w - s.wz) * inv_dt, o.gz);
+    if (M.motor_clip) {
+        float T[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float t = M.Ginv[4 * r + 0] * F + M.Ginv[4 * r + 1] * tx + M.Ginv[4 * r + 2] * ty +
+                            M.Ginv[4 * r + 3] * tz;
+            T[r] = fminf(fmaxf(t, M.T_min), M.T_max);
+        }
+        F = (T[0] + T[1]) + (T[2] + T[3]);
+        tx = M.a * ((T[1] + T[2]) - (T[0] + T[3]));
+        ty = M.a * ((T[1] + T[3]) - (T[0] + T[2]));
+        tz = M.c_tf * ((T[2] + T[3]) - (T[0] + T[1]));
+    }
+    o.F = F;
+    o.tx = tx;
+    o.ty = ty;
+    o.tz = tz;
+    return o;
+}
+
+// ------------------------------------------------------------------- cost
+
+// rho_ref of Sec. IV-C against one padded reference row (16 floats).
+// The compensation terms c hold minus the low-order parts of p and v.
+__device__ __forceinline__ float tracking_cost(const DevCost& C, const State& x, const Comp& c, const float4* row) {
+    const float4 r0 = row[0], r1 = row[1], r2 = row[2], r3 = row[3];
+    const float dpx = (x.px - r0.x) - c.px, dpy = (x.py - r0.y) - c.py, dpz = (x.pz - r0.z) - c.pz;
+    const float dvx = (x.vx - r1.w) - c.vx, dvy = (x.vy - r2.x) - c.vy, dvz = (x.vz - r2.y) - c.vz;
+    const float dwx = x.wx - r2.z, dwy = x.wy - r2.w, dwz = x.wz - r3.x;
+    const float dot = x.qw * r0.w + x.qx * r1.x + x.qy * r1.y + x.qz * r1.z;
+    float d;
+    if (C.quat_metric == 0) {
+        d = 1.0f - dot * dot;
+    } else {
+        d = acosf(fminf(fmaxf(2.0f * dot * dot - 1.0f, -1.0f), 1.0f));
+    }
+    const float ep = fmaf(dpx, dpx, fmaf(dpy, dpy, dpz * dpz));
+    const float ev = fmaf(dvx, dvx, fmaf(dvy, dvy, dvz * dvz));
+    const float ew = fmaf(dwx, dwx, fmaf(dwy, dwy, dwz * dwz));
+    return fmaf(C.c_p, ep, fmaf(C.c_q, d * d, fmaf(C.c_v, ev, C.c_w * ew)));
+}
+
+// Obstacle term of Sec. IV-D at position p (origin-shifted): returns the
+// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)) and sets *hit when the
+// state is in collision (the indicator, counted once per state by the
+// caller as an exact integer).  With LANES lanes per sample each lane
+// takes every LANES-th obstacle and the group combines by xor-shuffles
+// (all lanes end with bitwise identical results).
+template <int LANES>
+__device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float py, float pz, const float4* so,
+                                               int M, int lane, int* hit_out) {
+    float bar = 0.0f;
+    bool hit = false;
+#pragma unroll 4
+    for (int o = lane; o < M; o += LANES) {
+        const float4 ob = so[o];
+        const float dx = px - ob.x, dy = py - ob.y, dz = pz - ob.z;
+        const float sph = ob.w >= 0.0f ? dz : 0.0f;  // vertical cylinders ignore z
+        const float s = fmaf(dx, dx, fmaf(dy, dy, sph * dz)) - fabsf(ob.w);
+        bar += exp2f(-C.beta_log2e * fmaxf(s, 0.0f));
+        hit |= (s <= 0.0f);
+    }
+    if (LANES > 1) {
+        unsigned h = hit ? 1u : 0u;
+#pragma unroll
+        for (int off = LANES / 2; off > 0; off >>= 1) {
+            bar += __shfl_xor_sync(0xffffffffu, bar, off, LANES);
+            h |= __shfl_xor_sync(0xffffffffu, h, off, LANES);
+        }
+        hit = h != 0u;
+    }
+    *hit_out += hit ? 1 : 0;
+    return C.c_bar * bar;
+}
+
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
+    const float y = v - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// ------------------------------------------------------------ TMA + mbarrier
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// Bounded wait on one phase of the barrier: ~seconds at most, then false.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    for (long long i = 0; i < (1ll << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ------------------------------------------------------------ block helpers
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Dynamic shared memory layout (byte offsets), identical on host and device.
+struct SmemLayout {
+    unsigned obs, ref, u, S, e, list, part, total;
+};
+
+__host__ __device__ inline unsigned align_up(unsigned v, unsigned a) { return (v + a - 1) / a * a; }
+
+__host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int block, int lanes) {
+    SmemLayout L;
+    const int spb = block / lanes;
+    const int npart = block > N_max ? block : N_max;
+    unsigned o = 0;
+    L.obs = o;  o = align_up(o + 16u * (unsigned)M_max, 128);
+    L.ref = o;  o = align_up(o + 64u * (unsigned)(N_max + 1), 128);
+    L.u = o;    o = align_up(o + 16u * (unsigned)N_max, 128);
+    L.S = o;    o = align_up(o + 8u * (unsigned)spb, 128);
+    L.e = o;    o = align_up(o + 4u * (unsigned)spb, 128);
+    L.list = o; o = align_up(o + 4u * (unsigned)spb, 128);
+    L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
+    L.total = o;
+    return L;
+}
+
+// Weight below which exp(-x) is zero in FP32 (denormals included): such
+// samples contribute exactly nothing and are skipped.
+constexpr float kMaxExpArg = 104.0f;
+
+// --------------------------------------------------------------- the kernel
+
+template <int LANES>
+__global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ DevInstance sI;
+    __shared__ int s_tile, s_inst, s_tile_in_inst, s_last, s_count;
+    __shared__ float s_x0[16], s_xhat[13], s_eta;
+    __shared__ double s_rho;
+    __shared__ double s_redd[32];
+    __shared__ float s_red[32];
+
+    const int tid = threadIdx.x;
+    const int nthreads = blockDim.x;
+    const int spb = nthreads / LANES;
+    const int group = tid / LANES;
+    const int lane = tid % LANES;
+    const int warp = tid >> 5, wlane = tid & 31, nwarps = nthreads >> 5;
+
+    const SmemLayout L = smem_layout(a.N_max, a.M_max, nthreads, LANES);
+    float4* sobs = reinterpret_cast<float4*>(smem + L.obs);
+    float4* sref = reinterpret_cast<float4*>(smem + L.ref);
+    float4* su = reinterpret_cast<float4*>(smem + L.u);
+    double* sS = reinterpret_cast<double*>(smem + L.S);
+    float* sE = reinterpret_cast<float*>(smem + L.e);
+    int* slist = reinterpret_cast<int*>(smem + L.list);
+    float4* spart = reinterpret_cast<float4*>(smem + L.part);
+
+    const unsigned bar = smem_addr(&mbar);
+    unsigned phase = 0;
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+
+    const DevModel& Mdl = a.M;
+    const DevCost& C = a.C;
+    const int n_tiles = a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles;
+
+    for (int round = 0;; ++round) {
+        // ---------------------------------------------------- pick a tile
+        if (tid == 0) {
+            int t;
+            if (a.tile_counter) t = (int)atomicAdd(a.tile_counter, 1u);
+            else t = round == 0 ? (int)blockIdx.x : n_tiles;
+            s_tile = t;
+            if (t < n_tiles) {
+                const int2 tm = a.tile_map ? a.tile_map[t] : make_int2(0, t);
+                s_inst = tm.x;
+                s_tile_in_inst = tm.y;
+                sI = a.insts ? a.insts[tm.x] : a.single;
+            }
+        }
+        __syncthreads();
+        if (s_tile >= n_tiles) break;
+        const int inst = s_inst;
+        const int tile = s_tile_in_inst;
+        const int K = sI.K, N = sI.N, M = sI.M;
+        const float dt = sI.dt, inv_dt = 1.0f / sI.dt, lambda = sI.lambda;
+        const unsigned long long iter = sI.iter_dev ? *sI.iter_dev : sI.iter;
+        const unsigned key0 = sI.key0, key1 = sI.key1;
+        float sigma[4] = {sI.sigma[0], sI.sigma[1], sI.sigma[2], sI.sigma[3]};
+
+        // ---------------------------------- stage inputs in shared memory
+        // Obstacles by one bulk TMA copy (overlaps the loads below).
+        if (tid == 0 && M > 0) bulk_load(smem_addr(sobs), sI.obs, 16u * (unsigned)M, bar);
+        if (tid < 13) s_xhat[tid] = sI.x_hat[tid];
+        __syncthreads();
+        // Origin shift to the state estimate's position: translation
+        // invariant in exact arithmetic, keeps FP32 positions small.
+        const float p0x = s_xhat[0], p0y = s_xhat[1], p0z = s_xhat[2];
+        for (int j = tid; j <= N; j += nthreads) {
+            const float* r = sI.ref + 13 * (size_t)j;
+            sref[4 * j + 0] = make_float4(r[0] - p0x, r[1] - p0y, r[2] - p0z, r[3]);
+            sref[4 * j + 1] = make_float4(r[4], r[5], r[6], r[7]);
+            sref[4 * j + 2] = make_float4(r[8], r[9], r[10], r[11]);
+            sref[4 * j + 3] = make_float4(r[12], 0.0f, 0.0f, 0.0f);
+        }
+        for (int j = tid; j < N; j += nthreads) {
+            const float* u = sI.u_nom + 4 * (size_t)j;
+            su[j] = make_float4(u[0], u[1], u[2], u[3]);
+        }
+        if (tid == 0) {
+            State x;
+            x.px = 0.0f; x.py = 0.0f; x.pz = 0.0f;
+            x.qw = s_xhat[3]; x.qx = s_xhat[4]; x.qy = s_xhat[5]; x.qz = s_xhat[6];
+            x.vx = s_xhat[7]; x.vy = s_xhat[8]; x.vz = s_xhat[9];
+            x.wx = s_xhat[10]; x.wy = s_xhat[11]; x.wz = s_xhat[12];
+            if (C.delay > 0.0f) {
+                // Delay compensation (Sec. IV-E): predict x_hat forward.
+                const float* u = sI.u_nom;
+                const float4 u0 = clamp_input(Mdl, make_float4(u[0], u[1], u[2], u[3]));
+                const Feasible f = feasible(Mdl, x, u0, inv_dt);
+                rk4(Mdl, x, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, C.delay);
+            }
+            s_x0[0] = x.px; s_x0[1] = x.py; s_x0[2] = x.pz; s_x0[3] = x.qw; s_x0[4] = x.qx;
+            s_x0[5] = x.qy; s_x0[6] = x.qz; s_x0[7] = x.vx; s_x0[8] = x.vy; s_x0[9] = x.vz;
+            s_x0[10] = x.wx; s_x0[11] = x.wy; s_x0[12] = x.wz;
+        }
+        if (M > 0) {
+            if (!mbar_wait_bounded(bar, phase)) {
+                if (tid == 0) atomicOr(&a.errflags[inst], ERR_TIMEOUT);
+                mbar_wait_bounded(bar, phase);  // let the copy land before smem is reused
+            }
+            phase ^= 1u;
+            for (int o = tid; o < M; o += nthreads) {
+                const float4 ob = sobs[o];
+                const float reach = fabsf(ob.w) + C.r_uav;
+                const float rr = reach * reach;
+                sobs[o] = ob.w < 0.0f ? make_float4(ob.x - p0x, ob.y - p0y, 0.0f, -rr)
+                                      : make_float4(ob.x - p0x, ob.y - p0y, ob.z - p0z, rr);
+            }
+        }
+        __syncthreads();
+
+        // --------------------------------------------------- rollouts
+        const int k_raw = tile * spb + group;
+        const bool valid = k_raw < K;
+        const unsigned k = (unsigned)(valid ? k_raw : K - 1);
+        State x;
+        x.px = s_x0[0]; x.py = s_x0[1]; x.pz = s_x0[2]; x.qw = s_x0[3]; x.qx = s_x0[4];
+        x.qy = s_x0[5]; x.qz = s_x0[6]; x.vx = s_x0[7]; x.vy = s_x0[8]; x.vz = s_x0[9];
+        x.wx = s_x0[10]; x.wy = s_x0[11]; x.wz = s_x0[12];
+
+        // S_k = c_obs * (states in collision) + the continuous cost, kept
+        // apart: the indicator is an exact count and the continuous part a
+        // compensated FP32 sum, combined in FP64 only for the weights.
+        Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float S = 0.0f, Sc = 0.0f;
+        int nhit = 0;
+        kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
+                             obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, &nhit));
+        float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < N; ++j) {
+            const float4 d = noise_delta(normals4(k, (unsigned)j, iter, key0, key1), sigma);
+            const float4 un = su[j];
+            const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
+                                                          __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
+            float step = fmaf(C.R[0], u.x * u.x, fmaf(C.R[1], u.y * u.y, fmaf(C.R[2], u.z * u.z, C.R[3] * u.w * u.w)));
+            if (j > 0) {
+                const float ex = u.x - u_prev.x, ey = u.y - u_prev.y, ez = u.z - u_prev.z, ew = u.w - u_prev.w;
+                step += fmaf(C.Rd[0], ex * ex, fmaf(C.Rd[1], ey * ey, fmaf(C.Rd[2], ez * ez, C.Rd[3] * ew * ew)));
+            }
+            u_prev = u;
+            const Feasible f = feasible(Mdl, x, u, inv_dt);
+            rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
+            step += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
+            step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, &nhit);
+            kahan_add(S, Sc, step);
+        }
+        if (lane == 0) {
+            const double Sd = (double)C.c_obs * (double)nhit + ((double)S - (double)Sc);
+            if (valid && sI.costs) sI.costs[k_raw] = (float)Sd;
+            sS[group] = (valid && isfinite(Sd)) ? Sd : (double)INFINITY;
+        }
+        __syncthreads();
+
+        // ------------------------------------- tile min, weights, eta_t
+        if (warp == 0) {
+            double m = INFINITY;
+            for (int g = wlane; g < spb; g += 32) m = fmin(m, sS[g]);
+            m = warp_min_d(m);
+            if (wlane == 0) s_rho = m;
+        }
+        __syncthreads();
+        const double rho_t = s_rho;
+        for (int g = tid; g < spb; g += nthreads) {
+            const double sv = sS[g];
+            const float xarg = (float)((sv - rho_t) / (double)lambda);
+            sE[g] = (sv < INFINITY && xarg <= kMaxExpArg) ? expf(-xarg) : 0.0f;
+        }
+        __syncthreads();
+        // eta_t in a fixed order and the ascending list of contributors.
+        if (warp == 0) {
+            float acc = 0.0f;
+            for (int g = wlane; g < spb; g += 32) acc += sE[g];
+            acc = warp_sum(acc);
+            int base = 0;
+            for (int c0 = 0; c0 < spb; c0 += 32) {
+                const int g = c0 + wlane;
+                const bool on = g < spb && sE[g] > 0.0f;
+                const unsigned bal = __ballot_sync(0xffffffffu, on);
+                if (on) slist[base + __popc(bal & ((1u << wlane) - 1u))] = g;
+                base += __popc(bal);
+            }
+            if (wlane == 0) {
+                s_eta = acc;
+                s_count = base;
+            }
+        }
+        __syncthreads();
+
+        // ---------------------- weighted sum of the regenerated noise
+        // Threads (j, grp): grp-th share of the contributors for step j.
+        const int count = s_count;
+        {
+            const int G = N >= nthreads ? 1 : nthreads / N;
+            const int tile_base = tile * spb;
+            for (int w = tid; w < (N >= nthreads ? N : G * N); w += nthreads) {
+                const int j = w % N, grp = w / N;
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int ci = grp; ci < count; ci += G) {
+                    const int g = slist[ci];
+                    const float e = sE[g];
+                    const float4 d = noise_delta(normals4((unsigned)(tile_base + g), (unsigned)j, iter, key0, key1), sigma);
+                    acc.x = fmaf(e, d.x, acc.x);
+                    acc.y = fmaf(e, d.y, acc.y);
+                    acc.z = fmaf(e, d.z, acc.z);
+                    acc.w = fmaf(e, d.w, acc.w);
+                }
+                spart[grp * N + j] = acc;
+            }
+            __syncthreads();
+            float* P = a.partials + sI.part_off + (long long)tile * partial_stride(N);
+            for (int j = tid; j < N; j += nthreads) {
+                float4 s = spart[j];
+                for (int grp = 1; grp < G; ++grp) {
+                    const float4 t = spart[grp * N + j];
+                    s.x += t.x; s.y += t.y; s.z += t.z; s.w += t.w;
+                }
+                reinterpret_cast<float4*>(P + 4)[j] = s;
+            }
+            if (tid == 0) {
+                *reinterpret_cast<double*>(P) = rho_t;
+                P[2] = s_eta;
+                P[3] = 0.0f;
+            }
+        }
+
+        // ----------------------------- last tile of the instance merges
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(&a.done[inst], 1u);
+            s_last = (prev == (unsigned)(sI.n_tiles - 1)) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const int T = sI.n_tiles;
+            const int stride = partial_stride(N);
+            const float* P0 = a.partials + sI.part_off;
+            // rho = min rho_t (FP64 header of each partial)
+            double m = INFINITY;
+            for (int t = tid; t < T; t += nthreads)
+                m = fmin(m, __ldcg(reinterpret_cast<const double*>(P0 + (long long)t * stride)));
+            m = warp_min_d(m);
+            if (wlane == 0) s_redd[warp] = m;
+            __syncthreads();
+            if (warp == 0) {
+                double v = wlane < nwarps ? s_redd[wlane] : (double)INFINITY;
+                v = warp_min_d(v);
+                if (wlane == 0) s_rho = v;
+            }
+            __syncthreads();
+            const double rho = s_rho;
+            // s_t = exp(-(rho_t - rho)/lambda), kept in the partial's pad
+            // slot; eta = sum_t s_t eta_t.
+            float* Pw = a.partials + sI.part_off;
+            float eacc = 0.0f;
+            for (int t = tid; t < T; t += nthreads) {
+                const double rt = __ldcg(reinterpret_cast<const double*>(P0 + (long long)t * stride));
+                const float xarg = (float)((rt - rho) / (double)lambda);
+                const float st = (rt < INFINITY && xarg <= kMaxExpArg) ? expf(-xarg) : 0.0f;
+                __stcg(Pw + (long long)t * stride + 3, st);
+                eacc = fmaf(st, __ldcg(P0 + (long long)t * stride + 2), eacc);
+            }
+            eacc = warp_sum(eacc);
+            __syncthreads();
+            if (wlane == 0) s_red[warp] = eacc;
+            __syncthreads();
+            if (warp == 0) {
+                float v = wlane < nwarps ? s_red[wlane] : 0.0f;
+                v = warp_sum(v);
+                if (wlane == 0) s_eta = v;
+            }
+            __syncthreads();
+            const float eta = s_eta;
+            const bool ok = rho < INFINITY && eta > 0.0f;
+            const unsigned errs = a.errflags[inst];
+            // u_out = u_nom + Sigma / eta   (Eq. u_update)
+            float* sunew = reinterpret_cast<float*>(su);
+            for (int o = tid; o < 4 * N; o += nthreads) {
+                float acc = 0.0f;
+                if (ok) {
+                    for (int t = 0; t < T; ++t) {
+                        const float* Pt = P0 + (long long)t * stride;
+                        const float st = __ldcg(Pt + 3);
+                        if (st > 0.0f) acc = fmaf(st, __ldcg(Pt + 4 + o), acc);
+                    }
+                }
+                const float un = sI.u_nom[o];
+                const float v = ok ? un + acc / eta : un;
+                sunew[o] = v;
+                if (sI.u_out) sI.u_out[o] = v;
+            }
+            __syncthreads();
+            // Warm start: shift by alpha steps with linear interpolation.
+            if (sI.u_next) {
+                const float al = C.shift_alpha;
+                for (int o = tid; o < 4 * N; o += nthreads) {
+                    const int j = o >> 2, c = o & 3;
+                    const float later = (j + 1 < N) ? sunew[o + 4] : (C.tail_mode == 1 ? sunew[o] : Mdl.u_init[c]);
+                    sI.u_next[o] = al == 1.0f ? later : fmaf(al, later - sunew[o], sunew[o]);
+                }
+            }
+            if (tid == 0) {
+                // ApplyToSystem(u_nom_0): feasible command from x_hat.
+                State xh;
+                xh.px = s_xhat[0]; xh.py = s_xhat[1]; xh.pz = s_xhat[2]; xh.qw = s_xhat[3];
+                xh.qx = s_xhat[4]; xh.qy = s_xhat[5]; xh.qz = s_xhat[6]; xh.vx = s_xhat[7];
+                xh.vy = s_xhat[8]; xh.vz = s_xhat[9]; xh.wx = s_xhat[10]; xh.wy = s_xhat[11];
+                xh.wz = s_xhat[12];
+                const float4 u0 = clamp_input(Mdl, make_float4(sunew[0], sunew[1], sunew[2], sunew[3]));
+                const Feasible f = feasible(Mdl, xh, u0, inv_dt);
+                if (sI.u_cmd) {
+                    sI.u_cmd[0] = f.F;
+                    sI.u_cmd[1] = xh.wx + (f.tx - f.gx) * Mdl.inv_Jx * dt;
+                    sI.u_cmd[2] = xh.wy + (f.ty - f.gy) * Mdl.inv_Jy * dt;
+                    sI.u_cmd[3] = xh.wz + (f.tz - f.gz) * Mdl.inv_Jz * dt;
+                }
+                if (sI.x_next) {
+                    rk4(Mdl, xh, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz,
+                        C.shift_alpha * dt);
+                    const float v[13] = {xh.px, xh.py, xh.pz, xh.qw, xh.qx, xh.qy, xh.qz,
+                                         xh.vx, xh.vy, xh.vz, xh.wx, xh.wy, xh.wz};
+                    for (int i = 0; i < 13; ++i) sI.x_next[i] = v[i];
+                }
+                int st = MPPI_OK;
+                if (errs & ERR_TIMEOUT) st = MPPI_ETIMEOUT;
+                else if (!ok) st = MPPI_ENONFINITE;
+                if (sI.status) *sI.status = st;
+                if (sI.iter_dev) *sI.iter_dev = iter + 1ull;
+                a.done[inst] = 0u;
+                a.errflags[inst] = 0u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------- host
+
+bool shape_supported(Shape s) {
+    const bool lanes_ok = s.lanes == 1 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8;
+    const bool block_ok = s.block == 64 || s.block == 128 || s.block == 256 || s.block == 512;
+    return lanes_ok && block_ok;
+}
+
+size_t smem_bytes(int N_max, int M_max, Shape s) {
+    return smem_layout(N_max, M_max, s.block, s.lanes).total;
+}
+
+// Largest dynamic shared memory opted in so far, per instantiation.  The
+// attribute is raised only when a launch needs more, so launches that are
+// being captured into a graph (after a first, uncaptured preparation) make
+// no attribute call.
+template <int LANES>
+static std::atomic<int>& smem_opt_in() {
+    static std::atomic<int> v{0};
+    return v;
+}
+
+template <int LANES>
+static cudaError_t prepare_t(size_t smem) {
+    if ((int)smem <= smem_opt_in<LANES>().load()) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(mppi_step_kernel<LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess) {
+        int cur = smem_opt_in<LANES>().load();
+        while ((int)smem > cur && !smem_opt_in<LANES>().compare_exchange_weak(cur, (int)smem)) {
+        }
+    }
+    return e;
+}
+
+template <int LANES>
+static cudaError_t launch_t(const LaunchArgs& a, int block, int grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = prepare_t<LANES>(smem);
+    if (e != cudaSuccess) return e;
+    mppi_step_kernel<LANES><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tiles(const LaunchArgs& a, Shape s, int grid, size_t smem, cudaStream_t st) {
+    switch (s.lanes) {
+        case 1: return launch_t<1>(a, s.block, grid, smem, st);
+        case 2: return launch_t<2>(a, s.block, grid, smem, st);
+        case 4: return launch_t<4>(a, s.block, grid, smem, st);
+        case 8: return launch_t<8>(a, s.block, grid, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LANES>
+static int occupancy_t(int block, size_t smem) {
+    int n = 0;
+    prepare_t<LANES>(smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mppi_step_kernel<LANES>, block, smem) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+int max_active_blocks(Shape s, size_t smem) {
+    switch (s.lanes) {
+        case 1: return occupancy_t<1>(s.block, smem);
+        case 2: return occupancy_t<2>(s.block, smem);
+        case 4: return occupancy_t<4>(s.block, smem);
+        case 8: return occupancy_t<8>(s.block, smem);
+        default: return 1;
+    }
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace mppi

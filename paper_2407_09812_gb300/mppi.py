@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in include/mppi.h (libmppi_gb300.so).
+
+Argument marshalling only: every step of the MPPI iteration runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams; the
+binding passes raw device pointers.  There is no CPU fallback: when the
+library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmppi_gb300.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EAGAIN, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+N_MAX, M_MAX, K_MAX = 1024, 8192, 1 << 24
+
+
+class MppiError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+class Model(C.Structure):
+    _fields_ = [("mass", C.c_float), ("g", C.c_float), ("arm_l", C.c_float), ("c_tf", C.c_float),
+                ("J", C.c_float * 3), ("T_min", C.c_float), ("T_max", C.c_float), ("motor_clip", C.c_int32),
+                ("F_min", C.c_float), ("F_max", C.c_float), ("w_max", C.c_float * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("K", C.c_int32), ("N", C.c_int32), ("dt", C.c_float), ("lam", C.c_float),
+                ("sigma", C.c_float * 4), ("c_p", C.c_float), ("c_q", C.c_float), ("c_v", C.c_float),
+                ("c_w", C.c_float), ("R", C.c_float * 4), ("Rd", C.c_float * 4), ("c_obs", C.c_float),
+                ("c_bar", C.c_float), ("beta", C.c_float), ("r_uav", C.c_float), ("quat_metric", C.c_int32),
+                ("tail_mode", C.c_int32), ("shift_alpha", C.c_float), ("delay", C.c_float),
+                ("seed", C.c_uint64), ("stream_id", C.c_uint32), ("reserved", C.c_int32)]
+
+
+class Capacity(C.Structure):
+    _fields_ = [("max_instances", C.c_int32), ("max_samples", C.c_int64), ("N_max", C.c_int32),
+                ("M_max", C.c_int32)]
+
+
+class Instance(C.Structure):
+    _fields_ = [("x_hat", C.c_void_p), ("ref", C.c_void_p), ("obstacles", C.c_void_p), ("u_nom", C.c_void_p),
+                ("u_out", C.c_void_p), ("u_cmd", C.c_void_p), ("u_next", C.c_void_p), ("x_next", C.c_void_p),
+                ("costs", C.c_void_p), ("status", C.c_void_p), ("iter_dev", C.c_void_p), ("iter", C.c_uint64),
+                ("K", C.c_int32), ("N", C.c_int32), ("M", C.c_int32), ("dt", C.c_float), ("lam", C.c_float),
+                ("sigma", C.c_float * 4), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
+                ("reserved", C.c_int32)]
+
+
+class Shape(C.Structure):
+    _fields_ = [("block", C.c_int32), ("lanes", C.c_int32)]
+
+
+class ServerCfg(C.Structure):
+    _fields_ = [("max_vehicles", C.c_int32), ("slots", C.c_int32), ("max_batch", C.c_int32),
+                ("max_batch_samples", C.c_int64), ("N_max", C.c_int32), ("M_max", C.c_int32),
+                ("hbm_budget_bytes", C.c_int64), ("queue_capacity", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("request_id", C.c_uint64), ("vehicle", C.c_int32), ("status", C.c_int32),
+                ("u_cmd", C.c_float * 4), ("u0", C.c_float * 4), ("t_submit_us", C.c_double),
+                ("t_done_us", C.c_double), ("batch_size", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
+                ("batches", C.c_int64), ("bytes_in_use", C.c_int64), ("bytes_budget", C.c_int64),
+                ("busy_us", C.c_double)]
+
+
+_lib = None
+_VP = C.c_void_p
+_FP = C.POINTER(C.c_float)
+
+
+def lib():
+    """Loads the library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"MPPI CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    L.mppi_version.restype = C.c_char_p
+    L.mppi_strerror.restype = C.c_char_p
+    L.mppi_strerror.argtypes = [C.c_int]
+    L.mppi_create.argtypes = [C.POINTER(Model), C.POINTER(Params), C.POINTER(Capacity), C.POINTER(_VP)]
+    L.mppi_destroy.argtypes = [_VP]
+    L.mppi_destroy.restype = None
+    L.mppi_set_params.argtypes = [_VP, C.POINTER(Params)]
+    L.mppi_solve.argtypes = [_VP, _FP, _FP, _FP, C.c_int32, _FP, C.c_uint64, _FP, _FP, _FP, _FP, _FP]
+    L.mppi_solve_async.argtypes = [_VP, _VP, _VP, _VP, C.c_int32, _VP, C.c_uint64, _VP, _VP, _VP, _VP, _VP, _VP,
+                                   _VP]
+    L.mppi_solve_batch.argtypes = [_VP, C.POINTER(Instance), C.c_int32, _VP]
+    L.mppi_solve_batch_graph.argtypes = [_VP, C.POINTER(Instance), C.c_int32, _VP]
+    L.mppi_set_shape.argtypes = [_VP, C.POINTER(Shape)]
+    L.mppi_get_shape.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape)]
+    L.mppi_autotune.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape), _VP]
+    if hasattr(L, "mppi_server_create"):
+        L.mppi_server_create.argtypes = [C.POINTER(Model), C.POINTER(Params), C.POINTER(ServerCfg), C.POINTER(_VP)]
+        L.mppi_server_add_vehicle.argtypes = [_VP, C.c_int32, C.c_int32, C.c_float, C.c_float, _FP, _FP, C.c_int32,
+                                              _FP, C.c_uint64, C.c_uint32, C.POINTER(C.c_int32)]
+        L.mppi_server_remove_vehicle.argtypes = [_VP, C.c_int32]
+        L.mppi_server_submit.argtypes = [_VP, C.c_int32, _FP, _FP, C.POINTER(C.c_uint64)]
+        L.mppi_server_poll.argtypes = [_VP, C.POINTER(Result), C.c_int32, C.POINTER(C.c_int32)]
+        L.mppi_server_drain.argtypes = [_VP, C.c_int32]
+        L.mppi_server_export_vehicle.argtypes = [_VP, C.c_int32, _FP, C.POINTER(C.c_uint64)]
+        L.mppi_server_import_vehicle.argtypes = [_VP, C.c_int32, _FP, C.c_uint64]
+        L.mppi_server_get_stats.argtypes = [_VP, C.POINTER(ServerStats)]
+        L.mppi_server_destroy.argtypes = [_VP]
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().mppi_strerror(code).decode()
+    except RuntimeError:
+        return f"error {code}"
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise MppiError(rc, what)
+
+
+def make_model(m: dict) -> Model:
+    s = Model()
+    s.mass, s.g, s.arm_l, s.c_tf = m["mass"], m["g"], m["arm_l"], m["c_tf"]
+    s.J[:] = list(m["J"])
+    s.T_min, s.T_max, s.motor_clip = m["T_min"], m["T_max"], int(m["motor_clip"])
+    s.F_min, s.F_max = m["F_min"], m["F_max"]
+    s.w_max[:] = list(m["w_max"])
+    return s
+
+
+def make_params(p: dict) -> Params:
+    s = Params()
+    s.K, s.N, s.dt, s.lam = int(p["K"]), int(p["N"]), p["dt"], p["lambda"]
+    s.sigma[:] = list(p["sigma"])
+    s.c_p, s.c_q, s.c_v, s.c_w = p["c_p"], p["c_q"], p["c_v"], p["c_w"]
+    s.R[:] = list(p["R"])
+    s.Rd[:] = list(p["Rd"])
+    s.c_obs, s.c_bar, s.beta, s.r_uav = p["c_obs"], p["c_bar"], p["beta"], p["r_uav"]
+    s.quat_metric, s.tail_mode = int(p["quat_metric"]), int(p["tail_mode"])
+    s.shift_alpha, s.delay = p["shift_alpha"], p["delay"]
+    s.seed, s.stream_id, s.reserved = int(p["seed"]), int(p["stream_id"]), 0
+    return s
+
+
+def _fptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_FP)
+
+
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Solver:
+    """A handle: one vehicle model and one parameter set on the current
+    CUDA device, with its own device workspace."""
+
+    def __init__(self, model: dict, params: dict, capacity: dict | None = None):
+        self.model, self.params = dict(model), dict(params)
+        h = C.c_void_p()
+        cap = None
+        if capacity is not None:
+            cap = Capacity(int(capacity["max_instances"]), int(capacity["max_samples"]), int(capacity["N_max"]),
+                           int(capacity["M_max"]))
+        self._m, self._p = make_model(model), make_params(params)
+        _check(lib().mppi_create(C.byref(self._m), C.byref(self._p), C.byref(cap) if cap else None, C.byref(h)),
+               "mppi_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().mppi_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: dict):
+        self.params = dict(params)
+        self._p = make_params(params)
+        _check(lib().mppi_set_params(self.h, C.byref(self._p)), "mppi_set_params")
+
+    # ---------------------------------------------------------- host buffers
+    def solve(self, x_hat, ref, obstacles, u_nom, it: int, want_costs: bool = False) -> dict:
+        """mppi_solve: host numpy in, host numpy out (synchronous)."""
+        K, N = int(self.params["K"]), int(self.params["N"])
+        x = np.ascontiguousarray(x_hat, np.float32)
+        r = np.ascontiguousarray(ref, np.float32)
+        o = np.ascontiguousarray(obstacles, np.float32).reshape(-1, 4)
+        u = np.ascontiguousarray(u_nom, np.float32)
+        out = {"u_out": np.zeros((N, 4), np.float32), "u_cmd": np.zeros(4, np.float32),
+               "u_next": np.zeros((N, 4), np.float32), "x_next": np.zeros(13, np.float32),
+               "costs": np.zeros(K, np.float32) if want_costs else None}
+        rc = lib().mppi_solve(self.h, _fptr(x), _fptr(r), _fptr(o) if o.size else None, o.shape[0], _fptr(u), int(it),
+                              _fptr(out["u_out"]), _fptr(out["u_cmd"]), _fptr(out["u_next"]), _fptr(out["x_next"]),
+                              _fptr(out["costs"]))
+        if rc not in (OK, ENONFINITE):
+            raise MppiError(rc, "mppi_solve")
+        out["status"] = rc
+        return out
+
+    # -------------------------------------------------------- device buffers
+    def solve_async(self, x_hat, ref, obstacles, u_nom, it: int, u_out=None, u_cmd=None, u_next=None, x_next=None,
+                    costs=None, status=None, stream=None) -> None:
+        """mppi_solve_async: torch CUDA tensors in and out, enqueued on stream."""
+        M = 0 if obstacles is None else obstacles.numel() // 4
+        rc = lib().mppi_solve_async(self.h, _dptr(x_hat), _dptr(ref), _dptr(obstacles) if M else None, M,
+                                    _dptr(u_nom), int(it), _dptr(u_out), _dptr(u_cmd), _dptr(u_next), _dptr(x_next),
+                                    _dptr(costs), _dptr(status), _stream_ptr(stream))
+        _check(rc, "mppi_solve_async")
+
+    def solve_batch(self, instances: list, stream=None, graph: bool = False) -> None:
+        """mppi_solve_batch(_graph): instances are dicts of torch CUDA tensors
+        (x_hat, ref, obstacles, u_nom, and any of u_out, u_cmd, u_next,
+        x_next, costs, status, iter_dev) plus K, N, dt, lambda, sigma, seed,
+        stream_id, iter."""
+        arr = (Instance * len(instances))()
+        for i, d in enumerate(instances):
+            s = arr[i]
+            for f in ("x_hat", "ref", "u_nom", "u_out", "u_cmd", "u_next", "x_next", "costs", "status", "iter_dev"):
+                t = d.get(f)
+                setattr(s, f, t.data_ptr() if t is not None else None)
+            obs = d.get("obstacles")
+            M = 0 if obs is None else obs.numel() // 4
+            s.obstacles = obs.data_ptr() if M else None
+            s.iter = int(d.get("iter", 0))
+            s.K, s.N, s.M = int(d["K"]), int(d["N"]), M
+            s.dt, s.lam = float(d["dt"]), float(d["lambda"])
+            s.sigma[:] = list(d["sigma"])
+            s.seed, s.stream_id, s.reserved = int(d.get("seed", 0)), int(d.get("stream_id", 0)), 0
+        fn = lib().mppi_solve_batch_graph if graph else lib().mppi_solve_batch
+        _check(fn(self.h, arr, len(instances), _stream_ptr(stream)), "mppi_solve_batch")
+
+    # ---------------------------------------------------------- launch shape
+    def set_shape(self, block: int = 0, lanes: int = 0):
+        s = Shape(block, lanes)
+        _check(lib().mppi_set_shape(self.h, C.byref(s)), "mppi_set_shape")
+
+    def get_shape(self, K: int, N: int, M: int):
+        s = Shape()
+        _check(lib().mppi_get_shape(self.h, K, N, M, C.byref(s)), "mppi_get_shape")
+        return s.block, s.lanes
+
+    def autotune(self, K: int, N: int, M: int, stream=None):
+        s = Shape()
+        _check(lib().mppi_autotune(self.h, K, N, M, C.byref(s), _stream_ptr(stream)), "mppi_autotune")
+        return s.block, s.lanes
+
+
+def version() -> str:
+    return lib().mppi_version().decode()

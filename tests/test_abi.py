@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads without a GPU, exports every symbol the
+public header declares, and validates arguments on the host (no device
+work is queued for an invalid call)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2407_09812_gb300 import build as B
+    return B.build()
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mppi_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("mppi_create", "mppi_solve", "mppi_solve_async", "mppi_solve_batch", "mppi_destroy",
+                 "mppi_solve_batch_graph", "mppi_autotune"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = C.CDLL(built)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_validation_rejects_bad_arguments(built):
+    from paper_2407_09812_gb300 import inputs as I
+    from paper_2407_09812_gb300 import mppi
+    L = mppi.lib()
+    h = C.c_void_p()
+    good_m, good_p = I.model(), I.params()
+    cases = [
+        (dict(good_m, mass=0.0), good_p),
+        (dict(good_m, J=(1e-3, -1.0, 1e-3)), good_p),
+        (dict(good_m, T_min=5.0, T_max=1.0), good_p),
+        (dict(good_m, motor_clip=2), good_p),
+        (good_m, dict(good_p, K=0)),
+        (good_m, dict(good_p, N=mppi.N_MAX + 1)),
+        (good_m, dict(good_p, dt=0.0)),
+        (good_m, dict(good_p, **{"lambda": -1.0})),
+        (good_m, dict(good_p, sigma=(1.0, float("nan"), 1.0, 1.0))),
+        (good_m, dict(good_p, shift_alpha=0.0)),
+        (good_m, dict(good_p, quat_metric=3)),
+        (good_m, dict(good_p, c_p=float("inf"))),
+    ]
+    for m, p in cases:
+        mm, pp = mppi.make_model(m), mppi.make_params(p)
+        assert L.mppi_create(C.byref(mm), C.byref(pp), None, C.byref(h)) == mppi.EINVAL, (m, p)
+        assert not h.value
+    assert L.mppi_create(None, None, None, C.byref(h)) == mppi.EINVAL
+    assert L.mppi_solve(None, None, None, None, 0, None, 0, None, None, None, None, None) == mppi.EINVAL
+    assert L.mppi_solve_batch(None, None, 0, None) == mppi.EINVAL
+    assert mppi.strerror(mppi.ENONFINITE) == "every rollout cost was non-finite"
+
+
+def test_version_string(built):
+    from paper_2407_09812_gb300 import mppi
+    assert "sm_103a" in mppi.version()

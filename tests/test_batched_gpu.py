@@ -1,0 +1,127 @@
+"""Batched persistent launch: many uneven instances in one launch (plain and
+replayed from a CUDA graph) give, per instance, the oracle's result within
+tolerance and bitwise the same result as solving that instance alone with
+the same launch shape."""
+import numpy as np
+import pytest
+
+from parity import assert_step_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2407_09812_gb300 import build as B
+    B.build()
+    from paper_2407_09812_gb300 import mppi
+    return mppi
+
+
+def _uneven(inp, n=12, seed=7):
+    probs = inp.batched_uneven(n=n, seed=seed, K_range=(40, 3000), N_range=(1, 40), M_max=24)
+    for i, p in enumerate(probs):
+        if i % 3 == 0:
+            p["obstacles"] = np.zeros((0, 4), np.float32)
+        p["params"] = dict(p["params"], **{"lambda": float([1.0, 50.0, 400.0][i % 3])})
+    return probs
+
+
+def _device(prob, torch):
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    K, N = prob["params"]["K"], prob["params"]["N"]
+    d = {"x_hat": t(prob["x_hat"]), "ref": t(prob["ref"]), "u_nom": t(prob["u_nom"]),
+         "obstacles": t(prob["obstacles"]) if prob["obstacles"].size else None,
+         "u_out": torch.zeros(N, 4, device=dev), "u_cmd": torch.zeros(4, device=dev),
+         "u_next": torch.zeros(N, 4, device=dev), "x_next": torch.zeros(13, device=dev),
+         "costs": torch.zeros(K, device=dev), "status": torch.zeros(1, dtype=torch.int32, device=dev),
+         "K": K, "N": N, "dt": prob["params"]["dt"], "lambda": prob["params"]["lambda"],
+         "sigma": prob["params"]["sigma"], "seed": prob["params"]["seed"],
+         "stream_id": prob["params"]["stream_id"], "iter": prob["iter"]}
+    return d
+
+
+def _host(d):
+    return {k: d[k].cpu().numpy() for k in ("u_out", "u_cmd", "u_next", "x_next", "costs")} | {
+        "status": int(d["status"].item())}
+
+
+def _cap(probs):
+    return {"max_instances": len(probs), "max_samples": sum(p["params"]["K"] for p in probs),
+            "N_max": max(p["params"]["N"] for p in probs), "M_max": 64}
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_matches_oracle_and_alone(M, orc, inp, graph):
+    import torch
+    probs = _uneven(inp)
+    s = M.Solver(probs[0]["model"], probs[0]["params"], _cap(probs))
+    s.set_shape(128, 2)
+    insts = [_device(p, torch) for p in probs]
+    s.solve_batch(insts, graph=graph)
+    torch.cuda.synchronize()
+    batched = [_host(d) for d in insts]
+    # Alone, same launch shape.
+    alone_solver = M.Solver(probs[0]["model"], probs[0]["params"], _cap(probs))
+    alone_solver.set_shape(128, 2)
+    for p, b in zip(probs, batched):
+        alone_solver.set_params(p["params"])
+        d = _device(p, torch)
+        alone_solver.solve_async(d["x_hat"], d["ref"], d["obstacles"], d["u_nom"], p["iter"], u_out=d["u_out"],
+                                 u_cmd=d["u_cmd"], u_next=d["u_next"], x_next=d["x_next"], costs=d["costs"],
+                                 status=d["status"])
+        torch.cuda.synchronize()
+        a = _host(d)
+        for k in ("u_out", "u_cmd", "u_next", "x_next", "costs"):
+            assert np.array_equal(a[k], b[k]), (k, p["params"]["K"], p["params"]["N"])
+        ref = orc.mppi_step(p, n_threads=8)
+        assert b["status"] == 0
+        assert_step_close(p, b, ref)
+    s.close()
+    alone_solver.close()
+
+
+def test_graph_replay_with_changing_batches(M, orc, inp):
+    """One captured graph serves batches of different composition within the
+    same capacity bucket; descriptors are updated between replays."""
+    import torch
+    probs = _uneven(inp, n=10, seed=11)
+    s = M.Solver(probs[0]["model"], probs[0]["params"], _cap(probs))
+    for subset in (probs[:10], probs[3:7], probs[::2], probs[:10]):
+        insts = [_device(p, torch) for p in subset]
+        s.solve_batch(insts, graph=True)
+        torch.cuda.synchronize()
+        for p, d in zip(subset, insts):
+            assert_step_close(p, _host(d), orc.mppi_step(p, n_threads=8))
+    s.close()
+
+
+def test_device_counter_and_in_place_warm_start(M, orc, inp):
+    """Serving semantics: the nominal lives on the device and is replaced in
+    place by the shifted update; the Philox counter is read and advanced on
+    the device."""
+    import torch
+    probs = _uneven(inp, n=4, seed=5)
+    s = M.Solver(probs[0]["model"], probs[0]["params"], _cap(probs))
+    insts, iters = [], []
+    for p in probs:
+        d = _device(p, torch)
+        it = torch.tensor([p["iter"]], dtype=torch.int64, device="cuda")
+        d["iter_dev"] = it
+        d["u_next"] = d["u_nom"]  # in place
+        insts.append(d)
+        iters.append(it)
+    expect = [p for p in probs]
+    for step in range(3):
+        s.solve_batch(insts, graph=True)
+        torch.cuda.synchronize()
+        for i, (p, d) in enumerate(zip(expect, insts)):
+            ref = orc.mppi_step(p, n_threads=8)
+            got = _host(d)
+            assert_step_close(p, dict(got, u_next=d["u_nom"].cpu().numpy()), ref)
+            assert int(iters[i].item()) == p["iter"] + 1
+            expect[i] = dict(p, u_nom=d["u_nom"].cpu().numpy(), iter=p["iter"] + 1)
+    s.close()

@@ -1,0 +1,179 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several tiles and a ragged tail; the full-size configurations
+(closed loop K=16384 N=100 M=64; stress K=262144 N=200 M=1024) are checked
+on every output the oracle can compute at that size (all costs and the
+update for the closed loop; sampled costs plus the update identity for the
+stress case).
+"""
+import numpy as np
+import pytest
+
+from parity import COST_RTOL, U_RTOL, assert_step_close, compare_step, control_err, cost_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2407_09812_gb300 import build as B
+    B.build()
+    from paper_2407_09812_gb300 import mppi
+    mppi.lib()
+    return mppi
+
+
+def gpu_solve(M, prob, want_costs=True, shape=None):
+    s = M.Solver(prob["model"], prob["params"])
+    if shape:
+        s.set_shape(*shape)
+    out = s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"], want_costs=want_costs)
+    s.close()
+    return out
+
+
+def gpu_solve_device(M, prob, shape=None):
+    import torch
+    dev = torch.device("cuda")
+    K, N = prob["params"]["K"], prob["params"]["N"]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    x, r, u = t(prob["x_hat"]), t(prob["ref"]), t(prob["u_nom"])
+    o = t(prob["obstacles"]) if prob["obstacles"].size else None
+    out = {k: torch.zeros(n, dtype=torch.float32, device=dev) for k, n in
+           (("u_out", (N, 4)), ("u_cmd", 4), ("u_next", (N, 4)), ("x_next", 13), ("costs", K))}
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    s = M.Solver(prob["model"], prob["params"])
+    if shape:
+        s.set_shape(*shape)
+    s.solve_async(x, r, o, u, prob["iter"], status=status, **out)
+    torch.cuda.synchronize()
+    s.close()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["status"] = int(status.item())
+    return res
+
+
+def test_plain_hover_full_size(M, orc, inp):
+    prob = inp.plain_hover()  # K=1024, N=50, dt=0.02, box clamp
+    ref = orc.mppi_step(prob, n_threads=8)
+    g = gpu_solve(M, prob)
+    e = assert_step_close(prob, g, ref)
+    d = gpu_solve_device(M, prob)
+    assert_step_close(prob, d, ref)
+    for k in ("u_out", "u_next", "u_cmd", "x_next", "costs"):
+        assert np.array_equal(g[k], d[k]), k  # host and device entry points agree bitwise
+    print("plain hover errors", e)
+
+
+@pytest.mark.parametrize("K,N", [(1, 1), (7, 3), (129, 5), (1000, 17), (4097, 2), (300, 130)])
+def test_ragged_sizes(M, orc, inp, K, N):
+    prob = inp.plain_hover(K=K, N=N, dt=0.02, seed=K * 31 + N)
+    ref = orc.mppi_step(prob, n_threads=8)
+    assert_step_close(prob, gpu_solve(M, prob), ref)
+
+
+@pytest.mark.parametrize("lam", [1.0, 300.0, 3000.0])
+def test_obstacles_and_motor_limits(M, orc, inp, lam):
+    prob = inp.eight_with_spheres(K=2048, N=40, M=64, t0=1.3, **{"lambda": lam})
+    rng = np.random.default_rng(9)
+    pillars = inp.cylinders(rng, 16, (-20.0, -10.0, 0.0), (20.0, 10.0, 5.0), 0.3, 1.0)
+    prob["obstacles"] = np.ascontiguousarray(np.concatenate([prob["obstacles"], pillars]))
+    ref = orc.mppi_step(prob, n_threads=8)
+    e = assert_step_close(prob, gpu_solve(M, prob), ref)
+    print("obstacles lambda", lam, e, "ess", 1.0 / np.sum(ref["weights"] ** 2))
+
+
+def test_collisions_in_rollouts(M, orc, inp):
+    # Obstacles placed on the reference path so that many rollouts collide.
+    prob = inp.eight_with_spheres(K=1024, N=30, M=8, t0=0.0)
+    ref_path = prob["ref"][::4, 0:3]
+    obs = np.concatenate([ref_path[:8], np.full((8, 1), 0.5, np.float32)], axis=1).astype(np.float32)
+    obs[:, 1] += 0.7
+    prob["obstacles"] = np.ascontiguousarray(obs)
+    ref = orc.mppi_step(prob, n_threads=8)
+    assert np.mean(ref["min_gap"] <= 0) > 0.05
+    assert_step_close(prob, gpu_solve(M, prob), ref)
+
+
+def test_temperature_limits_and_zero_noise(M, orc, inp):
+    base = inp.eight_with_spheres(K=777, N=12, M=16, t0=2.0)
+    for over in ({"lambda": 1e-30}, {"lambda": 1e30}, {"sigma": (0.0, 0.0, 0.0, 0.0)}, {"K": 1}):
+        prob = dict(base, params=dict(base["params"], **over))
+        ref = orc.mppi_step(prob, n_threads=8)
+        g = gpu_solve(M, prob)
+        assert_step_close(prob, g, ref)
+        if "sigma" in over:
+            assert np.array_equal(g["u_out"], prob["u_nom"])
+
+
+@pytest.mark.parametrize("over", [{"quat_metric": 1}, {"tail_mode": 1}, {"shift_alpha": 0.25},
+                                  {"delay": 0.004}, {"lambda": 20.0, "shift_alpha": 0.1, "tail_mode": 1}])
+def test_step_options(M, orc, inp, over):
+    base = inp.eight_with_spheres(K=1500, N=25, M=20, t0=0.7)
+    prob = dict(base, params=dict(base["params"], **over))
+    ref = orc.mppi_step(prob, n_threads=8)
+    assert_step_close(prob, gpu_solve(M, prob), ref)
+
+
+def test_nonfinite_state_reports_and_keeps_nominal(M, inp):
+    prob = inp.plain_hover(K=256, N=10)
+    prob["x_hat"] = prob["x_hat"].copy()
+    prob["x_hat"][8] = np.nan
+    g = gpu_solve(M, prob)
+    assert g["status"] == M.ENONFINITE
+    assert np.array_equal(g["u_out"], prob["u_nom"])
+
+
+def test_every_launch_shape_matches_and_is_deterministic(M, orc, inp):
+    prob = inp.eight_with_spheres(K=3000, N=20, M=40, t0=3.0, **{"lambda": 500.0})
+    ref = orc.mppi_step(prob, n_threads=8)
+    for block in (64, 128, 256, 512):
+        for lanes in (1, 2, 4, 8):
+            a = gpu_solve(M, prob, shape=(block, lanes))
+            assert_step_close(prob, a, ref)
+            b = gpu_solve(M, prob, shape=(block, lanes))
+            for k in ("u_out", "costs", "u_cmd"):
+                assert np.array_equal(a[k], b[k]), (block, lanes, k)
+
+
+def test_closed_loop_full_size(M, orc, inp):
+    """K=16384, N=100, dt=0.01, 64 spheres, figure eight: five closed-loop
+    steps; at every step the oracle is fed the GPU's state and nominal."""
+    prob = inp.eight_with_spheres()
+    s = M.Solver(prob["model"], prob["params"])
+    x, u = prob["x_hat"].copy(), prob["u_nom"].copy()
+    traj = inp.Trajectory("eight")
+    worst = {}
+    for t in range(5):
+        step = dict(prob, x_hat=x, u_nom=u, ref=traj.window(0.01 * t, 100, 0.01), iter=t)
+        g = s.solve(step["x_hat"], step["ref"], step["obstacles"], step["u_nom"], t, want_costs=True)
+        ref = orc.mppi_step(step, n_threads=16)
+        e = assert_step_close(step, g, ref)
+        worst = {k: max(worst.get(k, 0), v) for k, v in e.items()}
+        x, u = g["x_next"], g["u_next"]
+    s.close()
+    print("closed loop worst", worst)
+
+
+def test_stress_full_size_sampled(M, orc, inp):
+    """K=262144, N=200, dt=0.005, 512 spheres + 512 pillars: sampled costs
+    against the oracle, and the update equals sum_k w_k delta_k with the
+    weights of the GPU's own costs (FP64) and the oracle's noise."""
+    prob = inp.stress_line()
+    g = gpu_solve(M, prob)
+    K = prob["params"]["K"]
+    ks = np.unique(np.concatenate([np.arange(0, K, K // 96), [K - 1], np.argsort(g["costs"])[:32]]))
+    c_orc, gap = orc.sample_costs(prob, ks, n_threads=16)
+    err, grazing = cost_err(g["costs"][ks], c_orc, gap)
+    assert err <= COST_RTOL, (err, grazing)
+    S = g["costs"].astype(np.float64)
+    rc, w = orc.weights(S, prob["params"]["lambda"])
+    nz = np.nonzero(w > 1e-30)[0]
+    upd = np.zeros((prob["params"]["N"], 4))
+    for k in nz:
+        upd += w[k] * np.array([orc.noise(prob["params"], prob["iter"], int(k), j) for j in range(prob["params"]["N"])])
+    expect = prob["u_nom"].astype(np.float64) + upd
+    assert control_err(g["u_out"], expect, prob["params"]["sigma"]) <= U_RTOL
+    print("stress: sampled cost err", err, "grazing", grazing, "contributors", nz.size)
