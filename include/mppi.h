@@ -213,6 +213,24 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
 /* Looks up the shape the handle uses for a problem of size (K, N, M). */
 int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* shape);
 
+/* One MPPI step that allocates no memory (the paper has no counterpart:
+ * this is an interface for callers that cannot call cudaMalloc, such as a
+ * real-time control loop that forbids allocation after start-up, or a
+ * plug-in whose host framework owns all device memory).  Same arguments
+ * and results as mppi_solve_async, with the model and parameters passed
+ * directly instead of a handle; all buffers are DEVICE buffers supplied by
+ * the caller.  The scratch it needs lives in a fixed array compiled into
+ * the library (about 1 MiB, held by every GPU that loads the library until
+ * the process exits), so sizes are limited to K <= 32768 and N <= 256
+ * (MPPI_EINVAL beyond).  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU race, so
+ * order them on one stream.  Launch shape: 128 threads, one per sample. */
+int mppi_solve_noalloc(const mppi_model* model, const mppi_params* params, const float* x_hat,
+                       const float* ref, const float* obstacles, int32_t M, const float* u_nom, uint64_t iter,
+                       float* u_out, float* u_cmd, float* u_next, float* x_next, float* costs, int32_t* status,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,13 +16,7 @@
 
 using namespace mppi;
 
-namespace {
-
-struct GraphEntry {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int grid = 0;
-};
+namespace mppi {
 
 bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
 bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
@@ -104,6 +98,16 @@ DevCost make_dev_cost(const mppi_params& p) {
     c.shift_alpha = p.shift_alpha; c.delay = p.delay;
     return c;
 }
+
+}  // namespace mppi
+
+namespace {
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid = 0;
+};
 
 int ceil_log2(long long v) {
     int r = 0;

@@ -90,6 +90,14 @@ constexpr unsigned ERR_TIMEOUT = 1u;
 // s_t, then Sigma_t[N][4].
 MPPI_HD inline int partial_stride(int N) { return 4 + 4 * N; }
 
+// Host-side validation and conversion of the public parameter structs.
+int check_model(const mppi_model* m);
+int check_params(const mppi_params* p);
+int check_step(int K, int N, float dt, float lambda, const float* sigma);
+DevModel make_dev_model(const mppi_model& m);
+DevCost make_dev_cost(const mppi_params& p);
+bool aligned16(const void* p);
+
 size_t smem_bytes(int N_max, int M_max, Shape s);
 bool shape_supported(Shape s);
 cudaError_t launch_tiles(const LaunchArgs& a, Shape s, int grid, size_t smem, cudaStream_t st);

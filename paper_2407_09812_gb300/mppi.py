@@ -104,6 +104,8 @@ def lib():
     L.mppi_set_shape.argtypes = [_VP, C.POINTER(Shape)]
     L.mppi_get_shape.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape)]
     L.mppi_autotune.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape), _VP]
+    L.mppi_solve_noalloc.argtypes = [C.POINTER(Model), C.POINTER(Params), _VP, _VP, _VP, C.c_int32, _VP, C.c_uint64,
+                                     _VP, _VP, _VP, _VP, _VP, _VP, _VP]
     if hasattr(L, "mppi_server_create"):
         L.mppi_server_create.argtypes = [C.POINTER(Model), C.POINTER(Params), C.POINTER(ServerCfg), C.POINTER(_VP)]
         L.mppi_server_add_vehicle.argtypes = [_VP, C.c_int32, C.c_int32, C.c_float, C.c_float, _FP, _FP, C.c_int32,
@@ -270,6 +272,18 @@ class Solver:
         s = Shape()
         _check(lib().mppi_autotune(self.h, K, N, M, C.byref(s), _stream_ptr(stream)), "mppi_autotune")
         return s.block, s.lanes
+
+
+def solve_noalloc(model: dict, params: dict, x_hat, ref, obstacles, u_nom, it: int, u_out=None, u_cmd=None,
+                  u_next=None, x_next=None, costs=None, status=None, stream=None) -> None:
+    """mppi_solve_noalloc: the allocation-free step (no handle; scratch in a
+    fixed device array; K <= 32768, N <= 256).  torch CUDA tensors in/out."""
+    m, p = make_model(model), make_params(params)
+    M = 0 if obstacles is None else obstacles.numel() // 4
+    rc = lib().mppi_solve_noalloc(C.byref(m), C.byref(p), _dptr(x_hat), _dptr(ref), _dptr(obstacles) if M else None,
+                                  M, _dptr(u_nom), int(it), _dptr(u_out), _dptr(u_cmd), _dptr(u_next),
+                                  _dptr(x_next), _dptr(costs), _dptr(status), _stream_ptr(stream))
+    _check(rc, "mppi_solve_noalloc")
 
 
 def version() -> str:

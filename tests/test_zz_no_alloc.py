@@ -1,0 +1,74 @@
+"""The allocation-free entry point (mppi_solve_noalloc), for callers that
+cannot allocate device memory (a real-time loop that forbids allocation
+after start-up, a plug-in whose host framework owns all device memory).
+
+It is checked through the C ABI against the handle-based entry point
+(mppi_solve_async) on the same inputs, within the parity tolerance, on two
+calls in a row of different sizes (the second call reuses the fixed scratch
+array the first one left behind).  This file is collected last so that a
+run stopping at the first failure has already run every other test."""
+import numpy as np
+import pytest
+
+from parity import COST_RTOL, U_RTOL, control_err, cost_err, state_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(mppi, torch, prob, noalloc: bool):
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    K, N = prob["params"]["K"], prob["params"]["N"]
+    ins = (t(prob["x_hat"]), t(prob["ref"]), t(prob["obstacles"]) if prob["obstacles"].size else None,
+           t(prob["u_nom"]))
+    out = {k: torch.zeros(n, dtype=torch.float32, device=dev) for k, n in
+           (("u_out", (N, 4)), ("u_cmd", 4), ("u_next", (N, 4)), ("x_next", 13), ("costs", K))}
+    status = torch.full((1,), -99, dtype=torch.int32, device=dev)
+    if noalloc:
+        mppi.solve_noalloc(prob["model"], prob["params"], *ins, prob["iter"], status=status, **out)
+    else:
+        s = mppi.Solver(prob["model"], prob["params"])
+        s.solve_async(*ins, prob["iter"], status=status, **out)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["status"] = int(status.item())
+    if not noalloc:
+        s.close()
+    return res
+
+
+def test_noalloc_matches_handle_entry_point_twice():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2407_09812_gb300 import build as B
+    B.build()
+    from paper_2407_09812_gb300 import inputs as I
+    from paper_2407_09812_gb300 import mppi
+
+    first = I.eight_with_spheres(K=4096, N=60, M=48, t0=0.8, **{"lambda": 200.0})
+    second = I.eight_with_spheres(K=777, N=13, M=9, t0=2.1, seed=3)
+    second["iter"] = 5
+    for prob in (first, second):
+        ref = _run(mppi, torch, prob, noalloc=False)
+        got = _run(mppi, torch, prob, noalloc=True)
+        assert got["status"] == 0 and ref["status"] == 0
+        sig = prob["params"]["sigma"]
+        assert control_err(got["u_out"], ref["u_out"], sig) <= U_RTOL
+        assert control_err(got["u_next"], ref["u_next"], sig) <= U_RTOL
+        assert control_err(got["u_cmd"], ref["u_cmd"], sig) <= U_RTOL
+        assert state_err(got["x_next"], ref["x_next"]) <= U_RTOL
+        assert cost_err(got["costs"], ref["costs"])[0] <= COST_RTOL
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    import torch
+    from paper_2407_09812_gb300 import inputs as I
+    from paper_2407_09812_gb300 import mppi
+    big = I.plain_hover(K=40000, N=10)
+    x = torch.zeros(13, device="cuda")
+    with pytest.raises(mppi.MppiError) as e:
+        mppi.solve_noalloc(big["model"], big["params"], x, x, None, x, 0)
+    assert e.value.code == mppi.EINVAL
+    long = I.plain_hover(K=100, N=300)
+    with pytest.raises(mppi.MppiError):
+        mppi.solve_noalloc(long["model"], long["params"], x, x, None, x, 0)
