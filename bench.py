@@ -283,8 +283,18 @@ def run_batched(args, reps=5):
 
 
 def run_serving(args):
+    """1000 vehicles at 100 Hz (about 100k requests/s offered, far above one
+    GPU's capacity) plus lighter fleets that show the latency below
+    saturation."""
     from paper_2407_09812_gb300 import serve
-    return serve.run_fleet(duration_s=args.serve_seconds, n_vehicles=args.serve_vehicles)
+    main = serve.run_fleet(duration_s=args.serve_seconds, n_vehicles=args.serve_vehicles)
+    sweep = []
+    for nv in (10, 100):
+        r = serve.run_fleet(duration_s=max(1.0, args.serve_seconds / 3), n_vehicles=nv, warmup_s=0.5)
+        sweep.append({k: r[k] for k in ("workload", "solves_per_s", "rollout_steps_per_s", "latency_ms",
+                                        "missed_ticks", "ticks", "mean_batch")})
+    main["lighter_fleets"] = sweep
+    return main
 
 
 def cpu_baseline(seconds: float):

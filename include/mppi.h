@@ -213,6 +213,91 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
 /* Looks up the shape the handle uses for a problem of size (K, N, M). */
 int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* shape);
 
+/* ---------------------------------------------------------------------
+ * Serving: continuous batching of solve requests from many vehicles.
+ * Each vehicle's nominal sequence and Philox counter stay on the device
+ * between its requests (warm start: the step's shifted nominal replaces
+ * the stored one, Alg. 1).  A dispatcher thread forms a batch from the
+ * queued requests whenever one of `slots` launch slots is free, so
+ * requests that arrive while earlier batches run are admitted as slots
+ * free up and their work overlaps on the device.  A vehicle has at most
+ * one request in flight; its later requests wait in the queue.  Vehicles
+ * are admitted against a device-memory budget that also covers the slots'
+ * workspaces.  All server entry points are thread safe.
+ * ------------------------------------------------------------------- */
+typedef struct mppi_server mppi_server;
+
+typedef struct {
+    int32_t max_vehicles;
+    int32_t slots;             /* batches in flight at once (one stream each) */
+    int32_t max_batch;         /* instances per batch                         */
+    int32_t N_max, M_max;      /* largest N and M of any vehicle              */
+    int32_t queue_capacity;    /* queued requests before MPPI_EAGAIN          */
+    int64_t max_batch_samples; /* sum of K per batch                          */
+    int64_t hbm_budget_bytes;  /* device bytes for vehicle state + slots      */
+    int32_t block, lanes;      /* launch shape; 0, 0: automatic               */
+} mppi_server_cfg;
+
+typedef struct {
+    uint64_t request_id;
+    int32_t vehicle;
+    int32_t status;            /* MPPI_OK or the step's error code            */
+    float u_cmd[4];            /* [F_clip, omega_clip] to the flight controller */
+    float u0[4];               /* updated nominal u_out_0                     */
+    double t_submit_us;        /* host steady clock, microseconds             */
+    double t_done_us;          /* when the dispatcher saw the batch complete  */
+    int32_t batch_size;        /* instances in the batch that served it       */
+    int32_t reserved;
+} mppi_result;
+
+typedef struct {
+    int64_t submitted, completed, rejected, batches, instances;
+    int64_t bytes_in_use, bytes_budget;
+    double busy_us;            /* sum over batches of launch-to-completion time */
+} mppi_server_stats;
+
+/* Creates a server on the current device for one vehicle model and one set
+ * of cost weights and options (params' K, N, dt, lambda, sigma, seed are
+ * unused: they are per vehicle).  MPPI_ENOMEM if the slots' workspaces do
+ * not fit the budget. */
+int mppi_server_create(const mppi_model* model, const mppi_params* params, const mppi_server_cfg* cfg,
+                       mppi_server** out);
+
+/* Registers a vehicle: sizes, temperature and noise, its obstacle set
+ * (host M*4, copied to the device), initial nominal (host N*4; NULL:
+ * hover) and Philox seed/stream.  MPPI_ENOMEM when its device state does
+ * not fit the remaining budget, MPPI_EINVAL for sizes beyond the config. */
+int mppi_server_add_vehicle(mppi_server* s, int32_t K, int32_t N, float dt, float lambda, const float* sigma,
+                            const float* obstacles, int32_t M, const float* u_init, uint64_t seed,
+                            uint32_t stream_id, int32_t* vehicle_id);
+
+/* Releases a vehicle and its device state once its requests are done. */
+int mppi_server_remove_vehicle(mppi_server* s, int32_t vehicle_id);
+
+/* Queues one solve request: state estimate x_hat[13] and reference window
+ * ref[(N+1)*13] (host, copied before return).  MPPI_EAGAIN when the queue
+ * is full, MPPI_ENOTFOUND for an unknown vehicle. */
+int mppi_server_submit(mppi_server* s, int32_t vehicle_id, const float* x_hat, const float* ref,
+                       uint64_t* request_id);
+
+/* Moves up to `max` completed results into out[] and sets *n. */
+int mppi_server_poll(mppi_server* s, mppi_result* out, int32_t max, int32_t* n);
+
+/* Waits until no request is queued or in flight (timeout_ms < 0: no
+ * limit); MPPI_ETIMEOUT if that did not happen in time. */
+int mppi_server_drain(mppi_server* s, int32_t timeout_ms);
+
+/* Copies a vehicle's device state (nominal N*4, Philox counter) to the
+ * host, or replaces it from the host (migration, checkpoint and resume).
+ * Both wait until the vehicle has nothing in flight. */
+int mppi_server_export_vehicle(mppi_server* s, int32_t vehicle_id, float* u_nom, uint64_t* iter);
+int mppi_server_import_vehicle(mppi_server* s, int32_t vehicle_id, const float* u_nom, uint64_t iter);
+
+int mppi_server_get_stats(mppi_server* s, mppi_server_stats* st);
+
+/* Stops the dispatcher after draining and frees everything. */
+int mppi_server_destroy(mppi_server* s);
+
 /* One MPPI step that allocates no memory (the paper has no counterpart:
  * this is an interface for callers that cannot call cudaMalloc, such as a
  * real-time control loop that forbids allocation after start-up, or a

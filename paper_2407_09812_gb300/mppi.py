@@ -59,9 +59,9 @@ class Shape(C.Structure):
 
 
 class ServerCfg(C.Structure):
-    _fields_ = [("max_vehicles", C.c_int32), ("slots", C.c_int32), ("max_batch", C.c_int32),
-                ("max_batch_samples", C.c_int64), ("N_max", C.c_int32), ("M_max", C.c_int32),
-                ("hbm_budget_bytes", C.c_int64), ("queue_capacity", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("max_vehicles", C.c_int32), ("slots", C.c_int32), ("max_batch", C.c_int32), ("N_max", C.c_int32),
+                ("M_max", C.c_int32), ("queue_capacity", C.c_int32), ("max_batch_samples", C.c_int64),
+                ("hbm_budget_bytes", C.c_int64), ("block", C.c_int32), ("lanes", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -72,8 +72,8 @@ class Result(C.Structure):
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
-                ("batches", C.c_int64), ("bytes_in_use", C.c_int64), ("bytes_budget", C.c_int64),
-                ("busy_us", C.c_double)]
+                ("batches", C.c_int64), ("instances", C.c_int64), ("bytes_in_use", C.c_int64),
+                ("bytes_budget", C.c_int64), ("busy_us", C.c_double)]
 
 
 _lib = None

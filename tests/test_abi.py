@@ -29,7 +29,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("mppi_create", "mppi_solve", "mppi_solve_async", "mppi_solve_batch", "mppi_destroy",
-                 "mppi_solve_batch_graph", "mppi_autotune"):
+                 "mppi_solve_batch_graph", "mppi_autotune", "mppi_server_create", "mppi_server_submit",
+                 "mppi_server_poll", "mppi_solve_noalloc"):
         assert must in names
 
 
@@ -72,3 +73,33 @@ def test_host_validation_rejects_bad_arguments(built):
 def test_version_string(built):
     from paper_2407_09812_gb300 import mppi
     assert "sm_103a" in mppi.version()
+
+
+def test_server_host_validation(built):
+    """Server configuration errors are caught on the host, before any
+    device work: bad sizes (EINVAL) and slot workspaces over the budget
+    (ENOMEM)."""
+    from paper_2407_09812_gb300 import inputs as I
+    from paper_2407_09812_gb300 import mppi
+    L = mppi.lib()
+    m, p = mppi.make_model(I.model()), mppi.make_params(I.params())
+    h = C.c_void_p()
+
+    def cfg(**over):
+        c = mppi.ServerCfg()
+        vals = dict(max_vehicles=4, slots=2, max_batch=8, N_max=50, M_max=16, queue_capacity=16,
+                    max_batch_samples=8192, hbm_budget_bytes=1 << 30, block=0, lanes=0)
+        vals.update(over)
+        for k, v in vals.items():
+            setattr(c, k, v)
+        return c
+
+    for bad in (dict(slots=0), dict(max_batch=0), dict(N_max=0), dict(N_max=mppi.N_MAX + 1), dict(M_max=-1),
+                dict(queue_capacity=0), dict(block=96, lanes=1), dict(block=128, lanes=3)):
+        c = cfg(**bad)
+        assert L.mppi_server_create(C.byref(m), C.byref(p), C.byref(c), C.byref(h)) == mppi.EINVAL, bad
+    c = cfg(hbm_budget_bytes=1 << 12)
+    assert L.mppi_server_create(C.byref(m), C.byref(p), C.byref(c), C.byref(h)) == mppi.ENOMEM
+    assert not h.value
+    assert L.mppi_server_submit(None, 0, None, None, None) == mppi.EINVAL
+    assert L.mppi_server_destroy(None) == mppi.EINVAL

@@ -1,0 +1,158 @@
+"""Serving loop (continuous batching, device-resident warm start).
+
+* a vehicle's result is the same served alone and served in a mix of many
+  vehicles whose requests arrive while other batches are on the GPU;
+* results match the FP64 oracle, and the device-resident nominal and
+  Philox counter advance exactly like the host-side warm start;
+* admission by device-memory budget and the queue's backpressure.
+"""
+import numpy as np
+import pytest
+
+from parity import U_RTOL, assert_step_close, control_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2407_09812_gb300 import build as B
+    B.build()
+    from paper_2407_09812_gb300 import serve
+    return serve
+
+
+def _fleet(inp, n, seed=3):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        K = int(rng.choice([300, 1000, 2500]))
+        N = int(rng.choice([10, 25, 40]))
+        M = int(rng.integers(0, 12))
+        ph = float(rng.uniform(0, 6))
+        ref = inp.Trajectory("eight", {"phase": ph}).window(0.0, N, 0.01)
+        x = ref[0].copy()
+        x[0:3] += rng.uniform(-0.5, 0.5, 3).astype(np.float32)
+        obs = inp.spheres(rng, M, (-20, -10, 0), (20, 10, 5), 0.3, 1.0)
+        p = inp.params(K=K, N=N, dt=0.01, seed=1000 + i, stream_id=i, **{"lambda": [1.0, 80.0][i % 2]})
+        out.append(inp.problem(inp.model(motor_clip=1), p, x, ref, obs, inp.hover_u(inp.model(), N), it=0))
+    return out
+
+
+def _server(S, inp, n, slots=3, max_batch=8, shape=(128, 2)):
+    return S.Server(inp.model(motor_clip=1), inp.params(),
+                    {"max_vehicles": n, "slots": slots, "max_batch": max_batch, "N_max": 40, "M_max": 16,
+                     "queue_capacity": 256, "max_batch_samples": 8 * 2500, "hbm_budget_bytes": 2 << 30,
+                     "block": shape[0], "lanes": shape[1]})
+
+
+def _add(srv, p):
+    pr = p["params"]
+    return srv.add_vehicle(pr["K"], pr["N"], pr["dt"], pr["lambda"], pr["sigma"], p["obstacles"], p["u_nom"],
+                           pr["seed"], pr["stream_id"])
+
+
+def _collect(srv, want):
+    got = {}
+    import time
+    t0 = time.time()
+    while len(got) < want and time.time() - t0 < 60:
+        for r in srv.poll():
+            got[r["request_id"]] = r
+    assert len(got) == want
+    return got
+
+
+def test_same_alone_and_in_the_mix_and_matches_oracle(S, orc, inp):
+    probs = _fleet(inp, 40)
+    target = 7
+    # Alone.
+    srv = _server(S, inp, 1)
+    v = _add(srv, probs[target])
+    rid = srv.submit(v, probs[target]["x_hat"], probs[target]["ref"])
+    alone = _collect(srv, 1)[rid]
+    srv.close()
+    # In the mix: 40 vehicles, each submits 3 requests back to back, so
+    # later requests arrive while earlier batches run on the 3 slots.
+    srv = _server(S, inp, 40)
+    vids = [_add(srv, p) for p in probs]
+    first = {}
+    for rep in range(3):
+        for i, p in enumerate(probs):
+            rid = srv.submit(vids[i], p["x_hat"], p["ref"])
+            if rep == 0:
+                first[i] = rid
+    res = _collect(srv, 120)
+    st = srv.stats()
+    srv.close()
+    mix = res[first[target]]
+    assert alone["status"] == 0 and mix["status"] == 0
+    # Same launch shape: bitwise identical; the stated tolerance in any case.
+    assert np.array_equal(alone["u_cmd"], mix["u_cmd"]) and np.array_equal(alone["u0"], mix["u0"])
+    assert st["batches"] >= 15 and st["completed"] == 120
+    assert max(r["batch_size"] for r in res.values()) > 1
+    for i in (0, 3, target, 20, 39):
+        ref = orc.mppi_step(probs[i], n_threads=8)
+        r = res[first[i]]
+        sig = probs[i]["params"]["sigma"]
+        assert control_err(r["u0"], ref["u_out"][0], sig) <= U_RTOL
+        assert control_err(r["u_cmd"], ref["u_cmd"], sig) <= U_RTOL
+
+
+def test_device_resident_warm_start_advances_like_the_host_loop(S, orc, inp):
+    probs = _fleet(inp, 3, seed=9)
+    srv = _server(S, inp, 3)
+    vids = [_add(srv, p) for p in probs]
+    state = [dict(p) for p in probs]
+    for step in range(3):
+        rids = [srv.submit(v, state[i]["x_hat"], state[i]["ref"]) for i, v in enumerate(vids)]
+        res = _collect(srv, 3)
+        for i, v in enumerate(vids):
+            ref = orc.mppi_step(state[i], n_threads=8)
+            r = res[rids[i]]
+            sig = state[i]["params"]["sigma"]
+            assert control_err(r["u0"], ref["u_out"][0], sig) <= U_RTOL
+            u_dev, it = srv.export_vehicle(v)
+            assert it == step + 1
+            assert control_err(u_dev, ref["u_next"], sig) <= U_RTOL
+            state[i] = dict(state[i], u_nom=u_dev, iter=it)
+    # Import resets a vehicle (resume from a checkpoint).
+    srv.import_vehicle(vids[0], probs[0]["u_nom"], 0)
+    rid = srv.submit(vids[0], probs[0]["x_hat"], probs[0]["ref"])
+    r = _collect(srv, 1)[rid]
+    ref = orc.mppi_step(probs[0], n_threads=8)
+    assert control_err(r["u0"], ref["u_out"][0], probs[0]["params"]["sigma"]) <= U_RTOL
+    srv.remove_vehicle(vids[2])
+    srv.close()
+
+
+def test_admission_budget_and_backpressure(S, inp):
+    from paper_2407_09812_gb300 import mppi
+    probs = _fleet(inp, 4, seed=1)
+    base = {"max_vehicles": 8, "slots": 1, "max_batch": 2, "N_max": 40, "M_max": 16, "queue_capacity": 3,
+            "max_batch_samples": 5000, "block": 128, "lanes": 1}
+    # A budget that holds the slot workspace but no vehicle state.
+    import paper_2407_09812_gb300.serve as serve_mod
+    lo, hi = 1 << 16, 2 << 30
+    while hi - lo > 1024:  # smallest budget the server accepts
+        mid = (lo + hi) // 2
+        try:
+            serve_mod.Server(inp.model(), inp.params(), dict(base, hbm_budget_bytes=mid)).close()
+            hi = mid
+        except mppi.MppiError as e:
+            assert e.code == mppi.ENOMEM
+            lo = mid
+    srv = serve_mod.Server(inp.model(), inp.params(), dict(base, hbm_budget_bytes=hi))
+    with pytest.raises(mppi.MppiError) as e:
+        _add(srv, probs[0])
+    assert e.value.code == mppi.ENOMEM
+    srv.close()
+    srv = serve_mod.Server(inp.model(), inp.params(), dict(base, hbm_budget_bytes=1 << 30))
+    v = _add(srv, probs[0])
+    accepted = [srv.submit(v, probs[0]["x_hat"], probs[0]["ref"]) for _ in range(40)]
+    assert any(a is None for a in accepted)  # queue full -> MPPI_EAGAIN
+    srv.drain(60000)
+    assert srv.stats()["rejected"] >= 1
+    srv.close()
