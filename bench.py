@@ -114,11 +114,13 @@ def dist_setup(n_gpus: int):
 
 
 def barrier_max(value: float, world: int) -> float:
+    """Largest value over the ranks (the slowest rank's time)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -128,7 +130,14 @@ def barrier(world: int):
         import torch
         import torch.distributed as dist
         dist.barrier()
-        torch.cuda.synchronize()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+
+
+def whole_job_rate(units_per_step_per_rank: float, steps: int, max_ms: float, world: int) -> float:
+    """Units processed by all ranks divided by the slowest rank's time
+    (replicas: every rank solves its own vehicle; weak scaling)."""
+    return world * units_per_step_per_rank * steps / (max_ms * 1e-3)
 
 
 # --------------------------------------------------------------- workload
@@ -369,7 +378,7 @@ def main():
     total_ms_max = barrier_max(total_ms, world)
     per_step = total_ms_max / args.steps
     steps_per_solve = K_HEAD * N_HEAD
-    value = world * steps_per_solve * args.steps / (total_ms_max * 1e-3)
+    value = whole_job_rate(steps_per_solve, args.steps, total_ms_max, world)
 
     if rank != 0:
         if world > 1:

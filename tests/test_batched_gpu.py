@@ -125,3 +125,17 @@ def test_device_counter_and_in_place_warm_start(M, orc, inp):
             assert int(iters[i].item()) == p["iter"] + 1
             expect[i] = dict(p, u_nom=d["u_nom"].cpu().numpy(), iter=p["iter"] + 1)
     s.close()
+
+
+def test_autotuner_picks_a_supported_shape_and_uses_it(M, orc, inp):
+    prob = inp.eight_with_spheres(K=3000, N=30, M=48, t0=0.4, **{"lambda": 100.0})
+    s = M.Solver(prob["model"], prob["params"])
+    before = s.get_shape(3000, 30, 48)
+    best = s.autotune(3000, 30, 48)
+    assert best[0] in (64, 128, 256, 512) and best[1] in (1, 2, 4, 8) and best[0] // best[1] >= 8
+    assert s.get_shape(3000, 30, 48) == best
+    assert s.get_shape(3000, 30, 0) == s.get_shape(3000, 30, 0)  # other buckets keep their default
+    out = s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"], want_costs=True)
+    assert_step_close(prob, out, orc.mppi_step(prob, n_threads=8))
+    s.close()
+    print("autotune", before, "->", best)

@@ -1,0 +1,51 @@
+"""Multi-GPU form of the benchmark: replicas only (vehicles are independent,
+the path has no exchange step).  The host logic — per-rank problem
+(distinct Philox stream, same workload), max-over-ranks timing and the
+whole-job rate — runs here as world-size-2 gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out):
+    import numpy as np
+    import torch.distributed as dist
+
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    prob = bench.headline_problem(rank)
+    local_ms = 10.0 + 5.0 * rank  # rank 1 is the slower replica
+    mx = bench.barrier_max(local_ms, world)
+    bench.barrier(world)
+    rate = bench.whole_job_rate(bench.K_HEAD * bench.N_HEAD, 4, mx, world)
+    out.put((rank, mx, rate, int(prob["params"]["stream_id"]), float(np.sum(prob["obstacles"]))))
+    dist.destroy_process_group()
+
+
+def test_replicas_reduce_max_and_whole_job_rate():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, mx0, rate0, sid0, obs0), (r1, mx1, rate1, sid1, obs1) = res
+    assert mx0 == mx1 == 15.0  # the slowest rank's time on every rank
+    assert rate0 == rate1 == pytest.approx(2 * 16384 * 100 * 4 / 15e-3)
+    assert sid0 != sid1  # independent noise streams per replica
+    assert obs0 == obs1  # same workload on every replica
