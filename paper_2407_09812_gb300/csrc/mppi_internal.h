@@ -37,6 +37,7 @@ struct DevCost {
     float c_p, c_q, c_v, c_w;
     float R[4], Rd[4];
     float c_obs, c_bar, beta_log2e, r_uav;
+    float cull;             // squared-gap beyond which the barrier is exactly 0 (FP32)
     int quat_metric, tail_mode;
     float shift_alpha, delay;
 };

@@ -59,12 +59,18 @@ __device__ __forceinline__ float4 normals4(unsigned k, unsigned j, unsigned long
                                            unsigned key1) {
     const uint4 r = philox4x32_10(make_uint4(k, j, (unsigned)iter, (unsigned)(iter >> 32)), key0, key1);
     const float u0 = uniform01(r.x), u1 = uniform01(r.y), u2 = uniform01(r.z), u3 = uniform01(r.w);
-    const float rad01 = sqrtf(-2.0f * logf(u0));
-    const float rad23 = sqrtf(-2.0f * logf(u2));
+    // -2 ln u > 0 for every u of the map (u < 1), so sqrt(x) = x rsqrt(x).
+    const float a01 = -2.0f * logf(u0), a23 = -2.0f * logf(u2);
+    const float rad01 = a01 * rsqrtf(a01);
+    const float rad23 = a23 * rsqrtf(a23);
+    // Angle 2 pi u taken as 2 pi u - pi in (-pi, pi), where the hardware
+    // sine/cosine are accurate to ~5e-7 absolute; cos and sin change sign.
+    const float t1 = fmaf(6.2831853071795865f, u1, -3.1415926535897932f);
+    const float t3 = fmaf(6.2831853071795865f, u3, -3.1415926535897932f);
     float s1, c1, s3, c3;
-    sincospif(2.0f * u1, &s1, &c1);
-    sincospif(2.0f * u3, &s3, &c3);
-    return make_float4(rad01 * c1, rad01 * s1, rad23 * c3, rad23 * s3);
+    __sincosf(t1, &s1, &c1);
+    __sincosf(t3, &s3, &c3);
+    return make_float4(-rad01 * c1, -rad01 * s1, -rad23 * c3, -rad23 * s3);
 }
 
 // delta = sigma o z, rounded once (no contraction) so that the rollout and
@@ -230,25 +236,75 @@ __device__ __forceinline__ float tracking_cost(const DevCost& C, const State& x,
     return fmaf(C.c_p, ep, fmaf(C.c_q, d * d, fmaf(C.c_v, ev, C.c_w * ew)));
 }
 
+// Order-preserving map of finite floats to unsigned keys (and back), so
+// that the warp's bounding box comes from hardware integer reductions.
+__device__ __forceinline__ unsigned float_key(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_float(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Obstacle term of Sec. IV-D at position p (origin-shifted): returns the
-// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)) and sets *hit when the
-// state is in collision (the indicator, counted once per state by the
-// caller as an exact integer).  With LANES lanes per sample each lane
-// takes every LANES-th obstacle and the group combines by xor-shuffles
-// (all lanes end with bitwise identical results).
+// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)) and counts the state
+// as colliding in *hit_out (the indicator is one per state, an exact
+// integer count kept by the caller).
+//
+// Exact culling: the warp's positions are bounded by a box (shuffles);
+// each lane tests one obstacle of a 32-obstacle chunk against the box and
+// an obstacle is skipped by the whole warp when, for every position in the
+// box, its squared gap exceeds the cut-off beyond which the FP32 barrier
+// term is exactly zero (and so it cannot be in collision either).  Kept
+// obstacles are processed in ascending order, so the sum equals the
+// uncut sum.  With LANES lanes per sample the lanes of a sample take every
+// LANES-th kept obstacle and combine by xor-shuffles (bitwise identical
+// results on all lanes of the sample).
 template <int LANES>
 __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float py, float pz, const float4* so,
-                                               int M, int lane, int* hit_out) {
+                                               int M, int lane, int wlane, int* wlist, int* hit_out) {
     float bar = 0.0f;
     bool hit = false;
-#pragma unroll 4
-    for (int o = lane; o < M; o += LANES) {
-        const float4 ob = so[o];
-        const float dx = px - ob.x, dy = py - ob.y, dz = pz - ob.z;
-        const float sph = ob.w >= 0.0f ? dz : 0.0f;  // vertical cylinders ignore z
-        const float s = fmaf(dx, dx, fmaf(dy, dy, sph * dz)) - fabsf(ob.w);
-        bar += exp2f(-C.beta_log2e * fmaxf(s, 0.0f));
-        hit |= (s <= 0.0f);
+    if (M > 0) {
+        const unsigned kx = float_key(px), ky = float_key(py), kz = float_key(pz);
+        const float lox = key_float(__reduce_min_sync(0xffffffffu, kx));
+        const float hix = key_float(__reduce_max_sync(0xffffffffu, kx));
+        const float loy = key_float(__reduce_min_sync(0xffffffffu, ky));
+        const float hiy = key_float(__reduce_max_sync(0xffffffffu, ky));
+        const float loz = key_float(__reduce_min_sync(0xffffffffu, kz));
+        const float hiz = key_float(__reduce_max_sync(0xffffffffu, kz));
+        for (int o0 = 0; o0 < M; o0 += 32) {
+            const int o = o0 + wlane;
+            bool keep = false;
+            if (o < M) {
+                const float4 ob = so[o];
+                const float ex = fmaxf(fmaxf(lox - ob.x, ob.x - hix), 0.0f);
+                const float ey = fmaxf(fmaxf(loy - ob.y, ob.y - hiy), 0.0f);
+                const float ez = ob.w >= 0.0f ? fmaxf(fmaxf(loz - ob.z, ob.z - hiz), 0.0f) : 0.0f;
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                keep = d2 <= (fabsf(ob.w) + C.cull) * 1.0001f;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, keep);
+            if (keep) wlist[__popc(mask & ((1u << wlane) - 1u))] = o;
+            __syncwarp();
+            const int cnt = __popc(mask);
+            for (int c = lane; c < cnt; c += LANES) {
+                const float4 ob = so[wlist[c]];
+                const float dx = px - ob.x, dy = py - ob.y, dz = pz - ob.z;
+                const float sph = ob.w >= 0.0f ? dz : 0.0f;  // vertical cylinders ignore z
+                const float s = fmaf(dx, dx, fmaf(dy, dy, sph * dz)) - fabsf(ob.w);
+                bar += ex2_ftz(-C.beta_log2e * fmaxf(s, 0.0f));
+                hit |= (s <= 0.0f);
+            }
+            __syncwarp();
+        }
     }
     if (LANES > 1) {
         unsigned h = hit ? 1u : 0u;
@@ -330,7 +386,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Dynamic shared memory layout (byte offsets), identical on host and device.
 struct SmemLayout {
-    unsigned obs, ref, u, S, e, list, part, total;
+    unsigned obs, ref, u, S, e, list, part, wlist, total;
 };
 
 __host__ __device__ inline unsigned align_up(unsigned v, unsigned a) { return (v + a - 1) / a * a; }
@@ -347,6 +403,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.e = o;    o = align_up(o + 4u * (unsigned)spb, 128);
     L.list = o; o = align_up(o + 4u * (unsigned)spb, 128);
     L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
+    L.wlist = o; o = align_up(o + 4u * (unsigned)block, 128);
     L.total = o;
     return L;
 }
@@ -383,6 +440,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
     float* sE = reinterpret_cast<float*>(smem + L.e);
     int* slist = reinterpret_cast<int*>(smem + L.list);
     float4* spart = reinterpret_cast<float4*>(smem + L.part);
+    int* wlist = reinterpret_cast<int*>(smem + L.wlist) + 32 * (threadIdx.x >> 5);
 
     const unsigned bar = smem_addr(&mbar);
     unsigned phase = 0;
@@ -485,7 +543,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
         float S = 0.0f, Sc = 0.0f;
         int nhit = 0;
         kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
-                             obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, &nhit));
+                             obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &nhit));
         float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int j = 0; j < N; ++j) {
             const float4 d = noise_delta(normals4(k, (unsigned)j, iter, key0, key1), sigma);
@@ -501,7 +559,8 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
             const Feasible f = feasible(Mdl, x, u, inv_dt);
             rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
             step += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
-            step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, &nhit);
+            step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, wlane, wlist,
+                                         &nhit);
             kahan_add(S, Sc, step);
         }
         if (lane == 0) {
