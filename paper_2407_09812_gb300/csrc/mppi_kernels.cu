@@ -280,29 +280,37 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
         const float hiy = key_float(__reduce_max_sync(0xffffffffu, ky));
         const float loz = key_float(__reduce_min_sync(0xffffffffu, kz));
         const float hiz = key_float(__reduce_max_sync(0xffffffffu, kz));
-        for (int o0 = 0; o0 < M; o0 += 32) {
-            const int o = o0 + wlane;
-            bool keep = false;
-            if (o < M) {
-                const float4 ob = so[o];
-                const float ex = fmaxf(fmaxf(lox - ob.x, ob.x - hix), 0.0f);
-                const float ey = fmaxf(fmaxf(loy - ob.y, ob.y - hiy), 0.0f);
-                const float ez = ob.w >= 0.0f ? fmaxf(fmaxf(loz - ob.z, ob.z - hiz), 0.0f) : 0.0f;
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                keep = d2 <= (fabsf(ob.w) + C.cull) * 1.0001f;
-            }
-            const unsigned mask = __ballot_sync(0xffffffffu, keep);
-            if (keep) wlist[__popc(mask & ((1u << wlane) - 1u))] = o;
+        auto keep_test = [&](int o) -> bool {
+            if (o >= M) return false;
+            const float4 ob = so[o];
+            const float ex = fmaxf(fmaxf(lox - ob.x, ob.x - hix), 0.0f);
+            const float ey = fmaxf(fmaxf(loy - ob.y, ob.y - hiy), 0.0f);
+            const float ez = ob.w >= 0.0f ? fmaxf(fmaxf(loz - ob.z, ob.z - hiz), 0.0f) : 0.0f;
+            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            return d2 <= (fabsf(ob.w) + C.cull) * 1.0001f;
+        };
+        auto term = [&](const float4 ob) {
+            const float dx = px - ob.x, dy = py - ob.y, dz = pz - ob.z;
+            const float sph = ob.w >= 0.0f ? dz : 0.0f;  // vertical cylinders ignore z
+            const float sg = fmaf(dx, dx, fmaf(dy, dy, sph * dz)) - fabsf(ob.w);
+            hit |= (sg <= 0.0f);
+            return ex2_ftz(-C.beta_log2e * fmaxf(sg, 0.0f));
+        };
+        // Two 32-obstacle chunks are tested at once; the kept indices go to
+        // the warp's list in ascending order and are then processed by a
+        // counted loop (every lane of a sample takes every LANES-th one).
+        const unsigned lt = (1u << wlane) - 1u;
+        for (int o0 = 0; o0 < M; o0 += 64) {
+            const bool k0 = keep_test(o0 + wlane);
+            const bool k1 = keep_test(o0 + 32 + wlane);
+            const unsigned m0 = __ballot_sync(0xffffffffu, k0);
+            const unsigned m1 = __ballot_sync(0xffffffffu, k1);
+            const int n0 = __popc(m0);
+            if (k0) wlist[__popc(m0 & lt)] = o0 + wlane;
+            if (k1) wlist[n0 + __popc(m1 & lt)] = o0 + 32 + wlane;
             __syncwarp();
-            const int cnt = __popc(mask);
-            for (int c = lane; c < cnt; c += LANES) {
-                const float4 ob = so[wlist[c]];
-                const float dx = px - ob.x, dy = py - ob.y, dz = pz - ob.z;
-                const float sph = ob.w >= 0.0f ? dz : 0.0f;  // vertical cylinders ignore z
-                const float s = fmaf(dx, dx, fmaf(dy, dy, sph * dz)) - fabsf(ob.w);
-                bar += ex2_ftz(-C.beta_log2e * fmaxf(s, 0.0f));
-                hit |= (s <= 0.0f);
-            }
+            const int cnt = n0 + __popc(m1);
+            for (int c = lane; c < cnt; c += LANES) bar += term(so[wlist[c]]);
             __syncwarp();
         }
     }
@@ -403,7 +411,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.e = o;    o = align_up(o + 4u * (unsigned)spb, 128);
     L.list = o; o = align_up(o + 4u * (unsigned)spb, 128);
     L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
-    L.wlist = o; o = align_up(o + 4u * (unsigned)block, 128);
+    L.wlist = o; o = align_up(o + 8u * (unsigned)block, 128);
     L.total = o;
     return L;
 }
@@ -440,7 +448,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
     float* sE = reinterpret_cast<float*>(smem + L.e);
     int* slist = reinterpret_cast<int*>(smem + L.list);
     float4* spart = reinterpret_cast<float4*>(smem + L.part);
-    int* wlist = reinterpret_cast<int*>(smem + L.wlist) + 32 * (threadIdx.x >> 5);
+    int* wlist = reinterpret_cast<int*>(smem + L.wlist) + 64 * (threadIdx.x >> 5);
 
     const unsigned bar = smem_addr(&mbar);
     unsigned phase = 0;
