@@ -126,6 +126,18 @@ void mppi_destroy(mppi_handle h);
  * for calls made afterwards. */
 int mppi_set_params(mppi_handle h, const mppi_params* params);
 
+/* Grid-based collision module (Sec. IV-D names occupancy maps as one way
+ * to test set membership): a dense occupancy grid in DEVICE memory,
+ * grid[(iz * ny + iy) * nx + ix] != 0 marking an occupied voxel that spans
+ * origin + voxel * ([ix, ix+1) x [iy, iy+1) x [iz, iz+1)); positions outside
+ * the grid are free.  A state inside an occupied voxel counts toward the
+ * same once-per-state collision indicator as the obstacles (c_obs).  The
+ * grid applies to every later solve of the handle (single and batched)
+ * and must stay valid and unchanged while they run; grid == NULL removes
+ * it.  MPPI_EINVAL for non-positive sizes or voxel, or non-finite origin. */
+int mppi_set_grid(mppi_handle h, const uint8_t* grid, int32_t nx, int32_t ny, int32_t nz, const float* origin,
+                  float voxel);
+
 /* One MPPI step with HOST buffers, synchronous (Alg. 1, body of the loop).
  *   x_hat[13]          state estimate x^ (host).
  *   ref[(N+1)*13]      reference x_ref_0..x_ref_N (host).

@@ -68,6 +68,14 @@ typedef struct {
     uint64_t seed;
     uint32_t stream_id;
     int pad1;
+    /* Occupancy voxel grid (a grid-based collision module, Sec. IV-D):
+     * grid[(iz * gy + iy) * gx + ix] != 0 marks an occupied voxel of edge
+     * g_voxel whose lowest corner is g_origin + voxel * (ix, iy, iz);
+     * positions outside the grid are free.  grid == NULL: no grid. */
+    const uint8_t* grid;
+    int gx, gy, gz, pad2;
+    double g_origin[3];
+    double g_voxel;
 } orc_params;
 
 /* ------------------------------------------------------------------------
@@ -400,6 +408,45 @@ double orc_obstacle_gap(const orc_params* P, const double p[3], const double o[4
     return d2 - reach * reach;
 }
 
+/* Voxel of position p in the occupancy grid: 1 if occupied, 0 if free or
+ * outside.  *face_gap (optional) gets the distance from p to the nearest
+ * face of its voxel across which occupancy changes (+inf if none), used
+ * by tests to flag positions on an occupancy boundary. */
+int orc_grid_occupied(const orc_params* P, const double p[3], double* face_gap)
+{
+    if (!P->grid) return 0;
+    int n[3] = {P->gx, P->gy, P->gz};
+    int idx[3];
+    double frac[3];
+    for (int a = 0; a < 3; ++a) {
+        double c = (p[a] - P->g_origin[a]) / P->g_voxel;
+        double f = floor(c);
+        idx[a] = (int)f;
+        frac[a] = c - f;
+    }
+    int inside = 1;
+    for (int a = 0; a < 3; ++a)
+        if (idx[a] < 0 || idx[a] >= n[a]) inside = 0;
+    int occ = inside ? P->grid[((size_t)idx[2] * P->gy + idx[1]) * P->gx + idx[0]] != 0 : 0;
+    if (face_gap) {
+        double best = INFINITY;
+        for (int a = 0; a < 3; ++a) {
+            for (int side = 0; side < 2; ++side) {
+                int nb[3] = {idx[0], idx[1], idx[2]};
+                nb[a] += side ? 1 : -1;
+                int nb_in = nb[0] >= 0 && nb[0] < n[0] && nb[1] >= 0 && nb[1] < n[1] && nb[2] >= 0 && nb[2] < n[2];
+                int nb_occ = nb_in ? P->grid[((size_t)nb[2] * P->gy + nb[1]) * P->gx + nb[0]] != 0 : 0;
+                if (nb_occ != occ) {
+                    double d = (side ? 1.0 - frac[a] : frac[a]) * P->g_voxel;
+                    if (d < best) best = d;
+                }
+            }
+        }
+        *face_gap = best;
+    }
+    return occ;
+}
+
 /* Obstacle cost of one state (Sec. IV-D): c_obs * 1[x in C_obs] (one
  * indicator per state), plus the exponential barrier of the reading
  * c_bar * exp(-beta * max(gap, 0)) summed over obstacles.  *min_gap gets
@@ -414,6 +461,13 @@ double orc_obstacle_cost(const orc_params* P, const double x[13], const double* 
         if (min_gap && s < *min_gap) *min_gap = s;
         barrier += P->c_bar * exp(-P->beta * (s > 0.0 ? s : 0.0));
         if (s <= 0.0) in_collision = 1;
+    }
+    if (P->grid) {
+        double face = INFINITY;
+        if (orc_grid_occupied(P, x, &face)) in_collision = 1;
+        /* A position within `face` of an occupancy boundary: reported in
+         * metres (the same grazing threshold applies). */
+        if (min_gap && face < *min_gap) *min_gap = face;
     }
     return barrier + (in_collision ? P->c_obs : 0.0);
 }

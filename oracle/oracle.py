@@ -55,7 +55,9 @@ class OrcParams(C.Structure):
                 ("c_w", C.c_double), ("R", C.c_double * 4), ("Rd", C.c_double * 4), ("c_obs", C.c_double),
                 ("c_bar", C.c_double), ("beta", C.c_double), ("r_uav", C.c_double),
                 ("quat_metric", C.c_int), ("tail_mode", C.c_int), ("shift_alpha", C.c_double),
-                ("delay", C.c_double), ("seed", C.c_uint64), ("stream_id", C.c_uint32), ("pad1", C.c_int)]
+                ("delay", C.c_double), ("seed", C.c_uint64), ("stream_id", C.c_uint32), ("pad1", C.c_int),
+                ("grid", C.c_void_p), ("gx", C.c_int), ("gy", C.c_int), ("gz", C.c_int), ("pad2", C.c_int),
+                ("g_origin", C.c_double * 3), ("g_voxel", C.c_double)]
 
 
 def make_model(m: dict) -> OrcModel:
@@ -79,6 +81,14 @@ def make_params(p: dict) -> OrcParams:
     s.quat_metric, s.tail_mode = int(p["quat_metric"]), int(p["tail_mode"])
     s.shift_alpha, s.delay = p["shift_alpha"], p["delay"]
     s.seed, s.stream_id = int(p["seed"]), int(p["stream_id"])
+    g = p.get("grid")
+    if g is not None:
+        occ = np.ascontiguousarray(g["occ"], np.uint8)  # shape (gz, gy, gx)
+        s._grid_ref = occ  # keep the buffer alive with the struct
+        s.grid = occ.ctypes.data
+        s.gz, s.gy, s.gx = occ.shape
+        s.g_origin[:] = list(g["origin"])
+        s.g_voxel = g["voxel"]
     return s
 
 
@@ -130,6 +140,8 @@ def lib():
                                        C.c_int, C.c_int, _D, _D]
         L.orc_noise_block.argtypes = [PP, C.c_uint64, C.c_int, C.c_int, _D]
         L.orc_max_threads.restype = C.c_int
+        L.orc_grid_occupied.restype = C.c_int
+        L.orc_grid_occupied.argtypes = [PP, _D, _D]
         _lib = L
     return _lib
 
@@ -327,6 +339,15 @@ def sample_costs(prob: dict, ks, n_threads: int = 1):
                            obs.size // 4, _p(u_nom), prob["iter"], ks.ctypes.data_as(C.POINTER(C.c_int)),
                            ks.size, n_threads, _p(out), _p(gap))
     return out, gap
+
+
+def grid_occupied(p: dict, pos):
+    """(occupied, distance to the nearest occupancy-changing voxel face)."""
+    P = make_params(p)
+    pos = _d(pos)
+    face = C.c_double()
+    occ = lib().orc_grid_occupied(C.byref(P), _p(pos), C.byref(face))
+    return occ, face.value
 
 
 def max_threads() -> int:

@@ -166,6 +166,13 @@ struct mppi_ctx {
     size_t io_floats = 0;
     cudaStream_t stream = nullptr;
 
+    // Occupancy grid applied to every solve of the handle (device pointer
+    // owned by the caller).
+    const unsigned char* grid = nullptr;
+    int gx = 0, gy = 0, gz = 0;
+    float g_origin[3] = {0, 0, 0};
+    float g_inv_voxel = 0;
+
     Shape forced{0, 0};
     std::map<uint64_t, Shape> table;
     std::map<uint64_t, GraphEntry> graphs;
@@ -502,12 +509,45 @@ void mppi_destroy(mppi_handle h) {
     delete h;
 }
 
+static void apply_grid(mppi_ctx* h) {
+    h->dc.grid = h->grid;
+    h->dc.gx = h->gx;
+    h->dc.gy = h->gy;
+    h->dc.gz = h->gz;
+    for (int a = 0; a < 3; ++a) h->dc.g_origin[a] = h->g_origin[a];
+    h->dc.g_inv_voxel = h->g_inv_voxel;
+}
+
 int mppi_set_params(mppi_handle h, const mppi_params* params) {
     if (!h) return MPPI_EINVAL;
     int rc = check_params(params);
     if (rc) return rc;
     h->params = *params;
     h->dc = make_dev_cost(*params);
+    apply_grid(h);
+    drop_graphs(h);
+    return MPPI_OK;
+}
+
+int mppi_set_grid(mppi_handle h, const uint8_t* grid, int32_t nx, int32_t ny, int32_t nz, const float* origin,
+                  float voxel) {
+    if (!h) return MPPI_EINVAL;
+    if (!grid) {
+        h->grid = nullptr;
+        h->gx = h->gy = h->gz = 0;
+    } else {
+        if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz > (1ll << 31) || !origin || !finite_pos(voxel))
+            return MPPI_EINVAL;
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(origin[a])) return MPPI_EINVAL;
+        h->grid = grid;
+        h->gx = nx;
+        h->gy = ny;
+        h->gz = nz;
+        for (int a = 0; a < 3; ++a) h->g_origin[a] = origin[a];
+        h->g_inv_voxel = (float)(1.0 / (double)voxel);
+    }
+    apply_grid(h);
     drop_graphs(h);
     return MPPI_OK;
 }

@@ -40,6 +40,12 @@ struct DevCost {
     float cull;             // squared-gap beyond which the barrier is exactly 0 (FP32)
     int quat_metric, tail_mode;
     float shift_alpha, delay;
+    // Occupancy voxel grid (NULL: none): grid[(iz*gy + iy)*gx + ix] != 0 is
+    // occupied; voxel (ix, iy, iz) spans origin + voxel * [i, i+1).
+    const unsigned char* grid;
+    int gx, gy, gz;
+    float g_origin[3];
+    float g_inv_voxel;
 };
 
 // One instance (vehicle problem) of a launch.

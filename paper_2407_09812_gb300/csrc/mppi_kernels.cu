@@ -254,9 +254,9 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 }
 
 // Obstacle term of Sec. IV-D at position p (origin-shifted): returns the
-// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)) and counts the state
-// as colliding in *hit_out (the indicator is one per state, an exact
-// integer count kept by the caller).
+// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)) and sets *hit_out when
+// the state is inside an obstacle (the indicator is one per state; the
+// caller keeps the count as an exact integer).
 //
 // Exact culling: the warp's positions are bounded by a box (shuffles);
 // each lane tests one obstacle of a 32-obstacle chunk against the box and
@@ -269,7 +269,7 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 // results on all lanes of the sample).
 template <int LANES>
 __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float py, float pz, const float4* so,
-                                               int M, int lane, int wlane, int* wlist, int* hit_out) {
+                                               int M, int lane, int wlane, int* wlist, bool* hit_out) {
     float bar = 0.0f;
     bool hit = false;
     if (M > 0) {
@@ -323,8 +323,19 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
         }
         hit = h != 0u;
     }
-    *hit_out += hit ? 1 : 0;
+    *hit_out = hit;
     return C.c_bar * bar;
+}
+
+// Grid-based collision module: is world position (wx, wy, wz) inside an
+// occupied voxel?  Outside the grid is free.
+__device__ __forceinline__ bool grid_hit(const DevCost& C, float wx, float wy, float wz) {
+    const int ix = (int)floorf((wx - C.g_origin[0]) * C.g_inv_voxel);
+    const int iy = (int)floorf((wy - C.g_origin[1]) * C.g_inv_voxel);
+    const int iz = (int)floorf((wz - C.g_origin[2]) * C.g_inv_voxel);
+    if ((unsigned)ix >= (unsigned)C.gx || (unsigned)iy >= (unsigned)C.gy || (unsigned)iz >= (unsigned)C.gz)
+        return false;
+    return __ldg(C.grid + ((size_t)iz * C.gy + iy) * C.gx + ix) != 0;
 }
 
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
@@ -550,8 +561,11 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
         Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float S = 0.0f, Sc = 0.0f;
         int nhit = 0;
+        bool hit = false;
         kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
-                             obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &nhit));
+                             obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &hit));
+        if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
+        nhit += hit ? 1 : 0;
         float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int j = 0; j < N; ++j) {
             const float4 d = noise_delta(normals4(k, (unsigned)j, iter, key0, key1), sigma);
@@ -568,7 +582,9 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
             rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
             step += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
             step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, wlane, wlist,
-                                         &nhit);
+                                         &hit);
+            if (C.grid) hit |= grid_hit(C, (x.px - cmp.px) + p0x, (x.py - cmp.py) + p0y, (x.pz - cmp.pz) + p0z);
+            nhit += hit ? 1 : 0;
             kahan_add(S, Sc, step);
         }
         if (lane == 0) {

@@ -96,6 +96,7 @@ def lib():
     L.mppi_destroy.argtypes = [_VP]
     L.mppi_destroy.restype = None
     L.mppi_set_params.argtypes = [_VP, C.POINTER(Params)]
+    L.mppi_set_grid.argtypes = [_VP, _VP, C.c_int32, C.c_int32, C.c_int32, _FP, C.c_float]
     L.mppi_solve.argtypes = [_VP, _FP, _FP, _FP, C.c_int32, _FP, C.c_uint64, _FP, _FP, _FP, _FP, _FP]
     L.mppi_solve_async.argtypes = [_VP, _VP, _VP, _VP, C.c_int32, _VP, C.c_uint64, _VP, _VP, _VP, _VP, _VP, _VP,
                                    _VP]
@@ -206,6 +207,18 @@ class Solver:
         self.params = dict(params)
         self._p = make_params(params)
         _check(lib().mppi_set_params(self.h, C.byref(self._p)), "mppi_set_params")
+
+    def set_grid(self, occ=None, origin=(0.0, 0.0, 0.0), voxel: float = 1.0):
+        """mppi_set_grid: occ is a torch uint8 CUDA tensor of shape (nz, ny, nx)
+        (kept referenced by the solver), or None to remove the grid."""
+        self._grid = occ
+        if occ is None:
+            _check(lib().mppi_set_grid(self.h, None, 0, 0, 0, None, 0.0), "mppi_set_grid")
+            return
+        nz, ny, nx = occ.shape
+        o = np.ascontiguousarray(origin, np.float32)
+        _check(lib().mppi_set_grid(self.h, C.c_void_p(occ.data_ptr()), nx, ny, nz, _fptr(o), float(voxel)),
+               "mppi_set_grid")
 
     # ---------------------------------------------------------- host buffers
     def solve(self, x_hat, ref, obstacles, u_nom, it: int, want_costs: bool = False) -> dict:

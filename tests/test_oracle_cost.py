@@ -136,3 +136,43 @@ def test_rollout_of_noise_uses_sample_noise_and_clamp(orc, inp):
     replay = dict(prob, params=quiet, u_nom=useq)  # float64 controls, no rounding
     S2, traj2, _, _ = orc.rollout(replay, 0, want_traj=True)
     assert np.allclose(traj, traj2, atol=1e-12) and math.isclose(S, S2, rel_tol=1e-12)
+
+
+def _grid_params(p):
+    occ = np.zeros((4, 5, 6), np.uint8)  # (z, y, x), voxel 0.5 m, origin (-1, -1, -1)
+    occ[2, 2, 3] = 1  # covers x in [0.5, 1), y in [0, 0.5), z in [0, 0.5)
+    return dict(p, grid={"occ": occ, "origin": (-1.0, -1.0, -1.0), "voxel": 0.5})
+
+
+def test_grid_occupancy_lookup(orc, inp):
+    p = _grid_params(inp.params())
+    assert orc.grid_occupied(p, (0.75, 0.25, 0.25))[0] == 1
+    assert orc.grid_occupied(p, (0.5, 0.0, 0.0))[0] == 1  # lower faces belong to the voxel
+    assert orc.grid_occupied(p, (1.0, 0.25, 0.25))[0] == 0  # upper face belongs to the next one
+    assert orc.grid_occupied(p, (0.25, 0.25, 0.25))[0] == 0
+    assert orc.grid_occupied(p, (0.25, 0.75, 0.25))[0] == 0  # swapped x/y would hit here
+    assert orc.grid_occupied(p, (0.25, 0.25, 0.75))[0] == 0  # swapped x/z would hit here
+    assert orc.grid_occupied(p, (5.0, 0.25, 0.25))[0] == 0  # outside the grid: free
+    assert orc.grid_occupied(p, (-1.25, 0.25, 0.25))[0] == 0
+    occ, face = orc.grid_occupied(p, (0.75, 0.3, 0.1))
+    assert occ == 1 and abs(face - 0.1) < 1e-12  # nearest occupancy-changing face is z = 0
+    occ, face = orc.grid_occupied(p, (-0.6, -0.6, -0.6))
+    assert occ == 0 and face == float("inf")  # neighbours all free
+
+
+@pytest.mark.parametrize("inside", [False, True])
+def test_grid_indicator_in_rollout_once_per_state(orc, inp, inside):
+    m, p = _quiet(inp, N=5)
+    N = p["N"]
+    p = _grid_params(p)
+    x = inp.state(p=(0.75, 0.25, 0.25) if inside else (0.25, 0.25, 0.25))
+    ref = inp.Trajectory("hover", {"at": tuple(x[:3])}).window(0.0, N, p["dt"])
+    u = inp.hover_u(m, N)
+    base = orc.rollout(inp.problem(m, dict(p, grid=None), x, ref, np.zeros((0, 4)), u), 0)
+    S = orc.rollout(inp.problem(m, p, x, ref, np.zeros((0, 4)), u), 0)
+    assert math.isclose(S - base, (N + 1) * p["c_obs"] if inside else 0.0, rel_tol=1e-12, abs_tol=1e-9)
+    # A sphere around the same state: still one indicator per state.
+    sph = np.array([[x[0], x[1], x[2], 0.3]], np.float32)
+    S2 = orc.rollout(inp.problem(m, p, x, ref, sph, u), 0)
+    S3 = orc.rollout(inp.problem(m, dict(p, grid=None), x, ref, sph, u), 0)
+    assert math.isclose(S2, S3, rel_tol=1e-12)

@@ -59,6 +59,10 @@ MUTANTS = [
                      "else later = u_init[c];")]),
     ("apply-old-nominal", [("orc_clamp_input(Mdl, &u_new[0], u0);", "orc_clamp_input(Mdl, &u_nom[0], u0);")]),
     ("delay-ignored", [("orc_rk4_step(Mdl, x_hat, F, tau, P->delay, x0);", "(void)0;")]),
+    ("grid-index-order", [("int occ = inside ? P->grid[((size_t)idx[2] * P->gy + idx[1]) * P->gx + idx[0]] != 0 : 0;",
+                           "int occ = inside ? P->grid[((size_t)idx[0] * P->gy + idx[1]) * P->gx + idx[2]] != 0 : 0;")]),
+    ("grid-rounding", [("double f = floor(c);", "double f = round(c);")]),
+    ("grid-ignored", [("if (orc_grid_occupied(P, x, &face)) in_collision = 1;", "orc_grid_occupied(P, x, &face);")]),
 ]
 
 

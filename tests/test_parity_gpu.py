@@ -177,3 +177,28 @@ def test_stress_full_size_sampled(M, orc, inp):
     expect = prob["u_nom"].astype(np.float64) + upd
     assert control_err(g["u_out"], expect, prob["params"]["sigma"]) <= U_RTOL
     print("stress: sampled cost err", err, "grazing", grazing, "contributors", nz.size)
+
+
+def test_grid_collision_module(M, orc, inp):
+    """Occupancy voxel grid as the collision module (with spheres too):
+    the GPU's per-state lookup and indicator match the oracle."""
+    import torch
+    prob = inp.eight_with_spheres(K=2048, N=40, M=16, t0=0.9, **{"lambda": 300.0})
+    rng = np.random.default_rng(21)
+    occ = (rng.uniform(size=(12, 44, 84)) < 0.02).astype(np.uint8)  # (z, y, x), 0.5 m voxels
+    origin, voxel = (-21.0, -11.0, -0.5), 0.5
+    # A wall of occupied voxels across the path ahead, so many rollouts hit it.
+    wx, wy, wz = ((prob["ref"][30, :3] - np.array(origin)) / voxel).astype(int)
+    occ[wz - 1:wz + 1, wy - 1:wy + 1, wx:wx + 1] = 1
+    prob["params"] = dict(prob["params"], grid={"occ": occ, "origin": origin, "voxel": voxel})
+    ref = orc.mppi_step(prob, n_threads=8)
+    assert np.mean(ref["costs"] >= prob["params"]["c_obs"]) > 0.05  # the grid is hit by many rollouts
+    s = M.Solver(prob["model"], prob["params"])
+    s.set_grid(torch.from_numpy(occ).cuda(), origin, voxel)
+    g = s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"], want_costs=True)
+    e = assert_step_close(prob, g, ref)
+    s.set_grid(None)
+    g2 = s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"], want_costs=True)
+    assert np.mean(g2["costs"] < g["costs"]) > 0.05  # removing the grid removes its penalties
+    s.close()
+    print("grid module errors", e)
