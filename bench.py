@@ -37,8 +37,11 @@ K_HEAD, N_HEAD, DT_HEAD, M_HEAD = 16384, 100, 0.01, 64
 WORKLOAD = ("closed-loop figure-eight tracking, K=16384, N=100, dt=0.01 s, 64 spheres, "
             "per-motor thrust limits, lambda=1")
 
-# Algorithmic FP32 work per rollout-step and per (state, obstacle) pair,
-# counted from the equations of the method ("Roofline").
+# Algorithmic FP32 work per rollout-step and per evaluated (state,
+# obstacle) pair, counted from the equations of the method (see the design doc,
+# "Roofline").  Pairs whose barrier term is exactly zero in FP32 and that
+# cannot be in collision are not part of the result and are not counted;
+# the kernel reports how many pairs it evaluated (mppi_set_counters).
 FLOP_PER_STEP = 650
 FLOP_PER_PAIR = 17
 SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
@@ -183,10 +186,14 @@ def run_closed_loop(args, rank):
         solver.solve_async(x[a], refs[i], obs, u[a], i, u_out=u_out, u_cmd=u_cmd, u_next=u[b], x_next=x[b],
                            status=status, stream=stream)
 
+    pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+    solver.set_counters(pairs)  # evaluated obstacle pairs, counted in the warm-up only
     for i in range(args.warmup):
         flush.zero_()
         step(i)
     torch.cuda.synchronize()
+    pairs_per_solve = int(pairs.item()) / args.warmup
+    solver.set_counters(None)
     barrier(args.world)
     with ClockSampler(torch.cuda.current_device()) as clk:
         wall0 = time.perf_counter()
@@ -203,7 +210,7 @@ def run_closed_loop(args, rank):
     final_x = x[n_total % 2].cpu().numpy()
     solver.close()
     return {"ms": ms, "wall": wall, "clocks": clk.summary(), "status": st, "final_x": final_x,
-            "x_trace_ok": bool(np.all(np.isfinite(final_x)))}
+            "x_trace_ok": bool(np.all(np.isfinite(final_x))), "pairs_per_solve": pairs_per_solve}
 
 
 def run_e2e(args, rank, n_steps):
@@ -258,6 +265,12 @@ def run_batched(args, reps=5):
     m = probs[0]["model"]
     solver = mppi.Solver(m, probs[0]["params"], cap)
     stream = torch.cuda.current_stream()
+    pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+    solver.set_counters(pairs)
+    solver.solve_batch(insts, stream=stream, graph=False)
+    torch.cuda.synchronize()
+    pairs_per_launch = int(pairs.item())
+    solver.set_counters(None)
     for _ in range(2):
         solver.solve_batch(insts, stream=stream, graph=True)
     torch.cuda.synchronize()
@@ -287,12 +300,52 @@ def run_batched(args, reps=5):
     ms_p = e0.elapsed_time(e1)
     plain.close()
     solver.close()
+    all_pairs = sum(i["K"] * (i["N"] + 1) * (0 if i["obstacles"] is None else i["obstacles"].shape[0])
+                    for i in insts)
+    flop = steps * FLOP_PER_STEP + pairs_per_launch * FLOP_PER_PAIR
     return {"workload": "256 uneven instances, K log-uniform [1024, 32768], N U[30,150], dt=0.01, 0-128 spheres",
             "instances": len(insts), "rollout_steps_per_launch": steps,
+            "obstacle_pairs": {"evaluated": pairs_per_launch, "all": all_pairs},
+            "method_tflops": flop / (ms_b * 1e-3) / 1e12,
+            "frac_of_fp32_peak": flop / (ms_b * 1e-3) / 1e12 / fp32_peak_tflops(),
             "batched_graph": {"ms_per_launch": ms_b, "rollout_steps_per_s": steps / (ms_b * 1e-3),
                               "solves_per_s": len(insts) / (ms_b * 1e-3)},
             "plain_sequential": {"ms_total": ms_p, "rollout_steps_per_s": steps / (ms_p * 1e-3),
                                  "solves_per_s": len(insts) / (ms_p * 1e-3)}}
+
+
+def run_stress(reps=3):
+    """K=262144, N=200, dt=0.005, 512 spheres + 512 pillars: one solve per
+    repetition on device buffers."""
+    import torch
+    from paper_2407_09812_gb300 import inputs as I
+    from paper_2407_09812_gb300 import mppi
+    dev = torch.device("cuda")
+    prob = I.stress_line()
+    K, N, M = prob["params"]["K"], prob["params"]["N"], prob["obstacles"].shape[0]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    x, r, o, u = t(prob["x_hat"]), t(prob["ref"]), t(prob["obstacles"]), t(prob["u_nom"])
+    u_out = torch.zeros(N, 4, device=dev)
+    s = mppi.Solver(prob["model"], prob["params"])
+    pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+    s.set_counters(pairs)
+    s.solve_async(x, r, o, u, 0, u_out=u_out)
+    torch.cuda.synchronize()
+    n_pairs = int(pairs.item())
+    s.set_counters(None)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(reps):
+        s.solve_async(x, r, o, u, i, u_out=u_out)
+    e1.record()
+    torch.cuda.synchronize()
+    s.close()
+    ms = e0.elapsed_time(e1) / reps
+    flop = K * N * FLOP_PER_STEP + n_pairs * FLOP_PER_PAIR
+    return {"workload": "K=262144, N=200, dt=0.005, 512 spheres + 512 vertical cylinders, 12 m/s line",
+            "ms_per_solve": ms, "rollout_steps_per_s": K * N / (ms * 1e-3),
+            "obstacle_pairs": {"evaluated": n_pairs, "all": K * (N + 1) * M},
+            "method_tflops": flop / (ms * 1e-3) / 1e12, "frac_of_fp32_peak": flop / (ms * 1e-3) / 1e12 / fp32_peak_tflops()}
 
 
 def run_serving(args):
@@ -342,6 +395,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-vehicles", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sections")
+    ap.add_argument("--section", default="all", choices=["all", "batched", "stress", "serving"],
+                    help="run one extra section alone and print its JSON (profiling aid)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args.gpus)
@@ -376,6 +431,11 @@ def main():
     from paper_2407_09812_gb300 import build as B
     B.build()
 
+    if args.section != "all":
+        fn = {"batched": lambda: run_batched(args), "stress": run_stress, "serving": lambda: run_serving(args)}
+        print(json.dumps({"section": args.section, **fn[args.section]()}), flush=True)
+        return
+
     res = run_closed_loop(args, rank)
     ms = res["ms"]
     total_ms = float(ms.sum())
@@ -389,7 +449,7 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
-    flop_launch = steps_per_solve * FLOP_PER_STEP + K_HEAD * (N_HEAD + 1) * M_HEAD * FLOP_PER_PAIR
+    flop_launch = steps_per_solve * FLOP_PER_STEP + res["pairs_per_solve"] * FLOP_PER_PAIR
     achieved = flop_launch / (float(ms.mean()) * 1e-3) / 1e12
     peak = fp32_peak_tflops()
     line = {
@@ -408,11 +468,15 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "mppi_step_kernel",
+                     "work": {"flop_per_rollout_step": FLOP_PER_STEP, "flop_per_obstacle_pair": FLOP_PER_PAIR,
+                              "obstacle_pairs_evaluated_per_solve": res["pairs_per_solve"],
+                              "obstacle_pairs_all_per_solve": K_HEAD * (N_HEAD + 1) * M_HEAD},
                      "peak_note": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
     }
     line["e2e"] = run_e2e(args, rank, n_steps=min(args.steps, 100))
     if not args.no_extras:
         line["batched"] = run_batched(args)
+        line["stress"] = run_stress()
         try:
             line["serving"] = run_serving(args)
         except (ImportError, AttributeError, OSError) as e:

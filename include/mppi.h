@@ -206,6 +206,14 @@ int mppi_solve_batch(mppi_handle h, const mppi_instance* instances, int32_t n, v
  * are updated in place between replays. */
 int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_t n, void* stream);
 
+/* Measurement hook (the paper has no counterpart): with a DEVICE counter
+ * set, every later launch of the handle adds to counters[0] the number of
+ * (rollout state, obstacle) pairs it evaluated after its exact culling
+ * (pairs whose barrier term is exactly zero in FP32 and that cannot be in
+ * collision are skipped).  Used to state the roofline in work actually
+ * required.  NULL turns it off.  The counter must be 8-byte aligned. */
+int mppi_set_counters(mppi_handle h, uint64_t* counters);
+
 /* Launch shape of the rollout kernel. */
 typedef struct {
     int32_t block;          /* threads per block: 64, 128, 256 or 512       */

@@ -173,6 +173,8 @@ struct mppi_ctx {
     float g_origin[3] = {0, 0, 0};
     float g_inv_voxel = 0;
 
+    unsigned long long* stats = nullptr;  // optional evaluated-pair counter (device)
+
     Shape forced{0, 0};
     std::map<uint64_t, Shape> table;
     std::map<uint64_t, GraphEntry> graphs;
@@ -309,6 +311,7 @@ LaunchArgs base_args(mppi_ctx* h, int n_inst) {
     LaunchArgs a;
     std::memset(&a, 0, sizeof(a));
     a.partials = h->partials;
+    a.stats = h->stats;
     a.done = h->counters + 1;
     a.errflags = h->counters + 1 + n_inst;
     a.M = h->dm;
@@ -548,6 +551,14 @@ int mppi_set_grid(mppi_handle h, const uint8_t* grid, int32_t nx, int32_t ny, in
         h->g_inv_voxel = (float)(1.0 / (double)voxel);
     }
     apply_grid(h);
+    drop_graphs(h);
+    return MPPI_OK;
+}
+
+int mppi_set_counters(mppi_handle h, uint64_t* counters) {
+    if (!h) return MPPI_EINVAL;
+    if (counters && (reinterpret_cast<uintptr_t>(counters) & 7u)) return MPPI_EINVAL;
+    h->stats = reinterpret_cast<unsigned long long*>(counters);
     drop_graphs(h);
     return MPPI_OK;
 }

@@ -83,6 +83,7 @@ struct LaunchArgs {
     unsigned* done;             // per-instance count of finished tiles
     unsigned* errflags;         // per-instance error bits
     const int* n_tiles_dev;     // device tile count (graph replay); NULL: n_tiles
+    unsigned long long* stats;  // optional: [0] += evaluated (state, obstacle) pairs
     int n_tiles;
     int n_inst;
     int N_max, M_max;           // sizes the dynamic shared memory was laid out for

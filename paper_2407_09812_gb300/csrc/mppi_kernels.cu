@@ -269,7 +269,8 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 // results on all lanes of the sample).
 template <int LANES>
 __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float py, float pz, const float4* so,
-                                               int M, int lane, int wlane, int* wlist, bool* hit_out) {
+                                               int M, int lane, int wlane, int* wlist, bool* hit_out,
+                                               unsigned* kept_out) {
     float bar = 0.0f;
     bool hit = false;
     if (M > 0) {
@@ -310,6 +311,7 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
             if (k1) wlist[n0 + __popc(m1 & lt)] = o0 + 32 + wlane;
             __syncwarp();
             const int cnt = n0 + __popc(m1);
+            *kept_out += (unsigned)cnt;
             for (int c = lane; c < cnt; c += LANES) bar += term(so[wlist[c]]);
             __syncwarp();
         }
@@ -562,8 +564,9 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
         float S = 0.0f, Sc = 0.0f;
         int nhit = 0;
         bool hit = false;
+        unsigned kept = 0;  // obstacles evaluated by this warp (uniform over the warp)
         kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
-                             obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &hit));
+                             obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &hit, &kept));
         if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
         nhit += hit ? 1 : 0;
         float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -582,10 +585,15 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
             rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
             step += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
             step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, wlane, wlist,
-                                         &hit);
+                                         &hit, &kept);
             if (C.grid) hit |= grid_hit(C, (x.px - cmp.px) + p0x, (x.py - cmp.py) + p0y, (x.pz - cmp.pz) + p0z);
             nhit += hit ? 1 : 0;
             kahan_add(S, Sc, step);
+        }
+        if (a.stats) {
+            // Evaluated pairs: kept obstacles x valid samples of this warp.
+            const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, valid && lane == 0));
+            if (wlane == 0 && kept) atomicAdd(a.stats, (unsigned long long)kept * nvalid);
         }
         if (lane == 0) {
             const double Sd = (double)C.c_obs * (double)nhit + ((double)S - (double)Sc);

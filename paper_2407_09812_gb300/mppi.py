@@ -97,6 +97,7 @@ def lib():
     L.mppi_destroy.restype = None
     L.mppi_set_params.argtypes = [_VP, C.POINTER(Params)]
     L.mppi_set_grid.argtypes = [_VP, _VP, C.c_int32, C.c_int32, C.c_int32, _FP, C.c_float]
+    L.mppi_set_counters.argtypes = [_VP, _VP]
     L.mppi_solve.argtypes = [_VP, _FP, _FP, _FP, C.c_int32, _FP, C.c_uint64, _FP, _FP, _FP, _FP, _FP]
     L.mppi_solve_async.argtypes = [_VP, _VP, _VP, _VP, C.c_int32, _VP, C.c_uint64, _VP, _VP, _VP, _VP, _VP, _VP,
                                    _VP]
@@ -219,6 +220,13 @@ class Solver:
         o = np.ascontiguousarray(origin, np.float32)
         _check(lib().mppi_set_grid(self.h, C.c_void_p(occ.data_ptr()), nx, ny, nz, _fptr(o), float(voxel)),
                "mppi_set_grid")
+
+    def set_counters(self, counters=None):
+        """mppi_set_counters: counters is a torch int64 CUDA tensor (>= 1
+        element) that later launches add their evaluated obstacle pairs to."""
+        self._counters = counters
+        _check(lib().mppi_set_counters(self.h, None if counters is None else C.c_void_p(counters.data_ptr())),
+               "mppi_set_counters")
 
     # ---------------------------------------------------------- host buffers
     def solve(self, x_hat, ref, obstacles, u_nom, it: int, want_costs: bool = False) -> dict:

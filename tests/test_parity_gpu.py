@@ -202,3 +202,25 @@ def test_grid_collision_module(M, orc, inp):
     assert np.mean(g2["costs"] < g["costs"]) > 0.05  # removing the grid removes its penalties
     s.close()
     print("grid module errors", e)
+
+
+def test_evaluated_pair_counter(M, orc, inp):
+    """The measurement hook counts evaluated (state, obstacle) pairs: all of
+    them when nothing can be culled (beta = 0: the barrier never vanishes),
+    fewer with the default barrier; the results stay within tolerance."""
+    import torch
+    prob = inp.eight_with_spheres(K=1000, N=20, M=40, t0=0.2)
+    for beta, exact in ((0.0, True), (1.0, False)):
+        p = dict(prob, params=dict(prob["params"], beta=beta))
+        s = M.Solver(p["model"], p["params"])
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        s.set_counters(cnt)
+        g = s.solve(p["x_hat"], p["ref"], p["obstacles"], p["u_nom"], p["iter"], want_costs=True)
+        s.close()
+        total = 1000 * 21 * 40
+        n = int(cnt.item())
+        if exact:
+            assert n == total
+        else:
+            assert 0 < n < total
+        assert_step_close(p, g, orc.mppi_step(p, n_threads=8))
