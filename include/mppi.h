@@ -219,6 +219,10 @@ typedef struct {
     int32_t block;          /* threads per block: 64, 128, 256 or 512       */
     int32_t lanes;          /* lanes per sample: 1 (one thread per sample),
                                2, 4 or 8 (warp split of the obstacle loop)  */
+    int32_t pipelined;      /* 1 (with lanes == 1): each sample has a
+                               dynamics thread and a cost thread in separate
+                               warps, handing states over through shared-
+                               memory rings (block/2 samples per block)     */
 } mppi_shape;
 
 /* Forces a launch shape for subsequent calls on the handle (both 0: back

@@ -123,13 +123,14 @@ uint64_t bucket_key(long long K, int N, int M) {
 }
 
 Shape default_shape(long long K, int N, int M) {
-    (void)K;
     (void)N;
-    (void)M;
-    // With the exact obstacle culling one thread per sample is fastest on
-    // every measured size (1k-262k samples, 0-1024 obstacles); the
-    // autotuner refines per size bucket.
-    return Shape{128, 1};
+    // Fewer 128-sample tiles than SMs and a real obstacle set: the step is
+    // bound by each warp's dependent chain, and the pipelined form (a
+    // dynamics and a cost thread per sample, separate warps) overlaps the
+    // obstacle scoring with the integration; otherwise one thread per
+    // sample.  The autotuner refines per size bucket.
+    if ((K + 127) / 128 < (long long)mppi::sm_count() && M >= 16) return Shape{256, 1, 1};
+    return Shape{128, 1, 0};
 }
 
 int bucket_pow2(int v, int lo) {
@@ -175,7 +176,7 @@ struct mppi_ctx {
 
     unsigned long long* stats = nullptr;  // optional evaluated-pair counter (device)
 
-    Shape forced{0, 0};
+    Shape forced{0, 0, 0};
     std::map<uint64_t, Shape> table;
     std::map<uint64_t, GraphEntry> graphs;
     cudaStream_t capture_stream = nullptr;
@@ -277,7 +278,8 @@ DevInstance make_instance(const mppi_ctx* h, const mppi_instance& in, Shape s) {
     d.iter_dev = reinterpret_cast<unsigned long long*>(in.iter_dev);
     d.iter = in.iter;
     d.K = in.K; d.N = in.N; d.M = in.M;
-    d.n_tiles = (in.K + s.block / s.lanes - 1) / (s.block / s.lanes);
+    const int spb = s.pipe ? s.block / (1 + s.lanes) : s.block / s.lanes;
+    d.n_tiles = (in.K + spb - 1) / spb;
     d.dt = in.dt; d.lambda = in.lambda;
     for (int c = 0; c < 4; ++c) d.sigma[c] = in.sigma[c];
     d.key0 = (unsigned)(in.seed & 0xffffffffu);
@@ -300,11 +302,13 @@ int check_instance(const mppi_instance& in, const mppi_ctx* h) {
     return MPPI_OK;
 }
 
-Shape choose_shape(const mppi_ctx* h, long long K, int N, int M) {
+// Tuned shape for the size bucket of (K, N, M), else the default for a
+// launch of K_total samples in all.
+Shape choose_shape(const mppi_ctx* h, long long K, int N, int M, long long K_total = -1) {
     if (h->forced.block) return h->forced;
     auto it = h->table.find(bucket_key(K, N, M));
     if (it != h->table.end()) return it->second;
-    return default_shape(K, N, M);
+    return default_shape(K_total < 0 ? K : K_total, N, M);
 }
 
 LaunchArgs base_args(mppi_ctx* h, int n_inst) {
@@ -358,8 +362,8 @@ int plan_batch(mppi_ctx* h, const mppi_instance* ins, int n, BatchPlan* plan) {
         Nmax = std::max(Nmax, ins[i].N);
         Mmax = std::max(Mmax, ins[i].M);
     }
-    Shape s = choose_shape(h, sumK / n, Nmax, Mmax);
-    const int spb = s.block / s.lanes;
+    Shape s = choose_shape(h, sumK / n, Nmax, Mmax, sumK);
+    const int spb = s.pipe ? s.block / (1 + s.lanes) : s.block / s.lanes;
     long long tiles = 0;
     size_t pf = 0;
     for (int i = 0; i < n; ++i) {
@@ -566,10 +570,10 @@ int mppi_set_counters(mppi_handle h, uint64_t* counters) {
 int mppi_set_shape(mppi_handle h, const mppi_shape* shape) {
     if (!h || !shape) return MPPI_EINVAL;
     if (shape->block == 0 && shape->lanes == 0) {
-        h->forced = Shape{0, 0};
+        h->forced = Shape{0, 0, 0};
         return MPPI_OK;
     }
-    Shape s{shape->block, shape->lanes};
+    Shape s{shape->block, shape->lanes, shape->pipelined};
     if (!shape_supported(s)) return MPPI_EINVAL;
     h->forced = s;
     return MPPI_OK;
@@ -580,6 +584,7 @@ int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* s
     Shape s = choose_shape(h, K, N, M);
     shape->block = s.block;
     shape->lanes = s.lanes;
+    shape->pipelined = s.pipe;
     return MPPI_OK;
 }
 
@@ -691,7 +696,7 @@ int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_
     const size_t smem = smem_bytes(plan.N_b, plan.M_b, plan.s);
     if (smem > 227 * 1024) return MPPI_EINVAL;
     const uint64_t key = ((uint64_t)plan.s.block << 48) | ((uint64_t)plan.s.lanes << 40) |
-                         ((uint64_t)plan.N_b << 20) | (uint64_t)plan.M_b;
+                         ((uint64_t)plan.s.pipe << 36) | ((uint64_t)plan.N_b << 20) | (uint64_t)plan.M_b;
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         GraphEntry g;
@@ -746,32 +751,33 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int blocks[] = {64, 128, 256, 512};
-    const int lanes[] = {1, 2, 4, 8};
-    Shape bestS{128, 1};
+    // Candidates: one thread or 2/4/8 lanes per sample (blocks 64-512), and
+    // the pipelined form with one or two cost lanes per sample.
+    std::vector<Shape> cands;
+    for (int b : {64, 128, 256, 512})
+        for (int l : {1, 2, 4, 8})
+            if (b / l >= 8) cands.push_back(Shape{b, l, 0});
+    for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 1});
+    for (int b : {192, 384}) cands.push_back(Shape{b, 2, 1});
+    Shape bestS{128, 1, 0};
     float bestT = 1e30f;
     int rc = MPPI_OK;
-    for (int b : blocks) {
-        for (int l : lanes) {
-            Shape s{b, l};
-            if (b / l < 8) continue;
-            if (smem_bytes(N, M, s) > 227 * 1024) continue;
-            if ((rc = launch_single(h, in, s, st))) break;  // warm-up
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < 3; ++r) launch_single(h, in, s, st);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                rc = MPPI_ECUDA;
-                break;
-            }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < bestT) {
-                bestT = ms;
-                bestS = s;
-            }
+    for (const Shape& s : cands) {
+        if (smem_bytes(N, M, s) > 227 * 1024) continue;
+        if ((rc = launch_single(h, in, s, st))) break;  // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) launch_single(h, in, s, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = MPPI_ECUDA;
+            break;
         }
-        if (rc) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < bestT) {
+            bestT = ms;
+            bestS = s;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -782,6 +788,7 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
     if (best) {
         best->block = bestS.block;
         best->lanes = bestS.lanes;
+        best->pipelined = bestS.pipe;
     }
     return MPPI_OK;
 }

@@ -72,6 +72,7 @@ struct DevInstance {
 struct Shape {
     int block;  // threads per block
     int lanes;  // lanes per sample
+    int pipe;   // 1: pipelined (a dynamics thread and a cost thread per sample)
 };
 
 // Everything one launch of the fused kernel needs.

@@ -385,6 +385,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
     return false;
 }
 
+// Bounded wait that also gives up when another warp of the block has
+// flagged an abort; a wait that runs out raises the flag itself, so a
+// stuck pipeline drains quickly instead of every later wait timing out.
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity, volatile int* abort_flag) {
+    for (long long i = 0; i < (1ll << 22); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 63 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // ------------------------------------------------------------ block helpers
 
 __device__ __forceinline__ float warp_min(float v) {
@@ -406,16 +422,22 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Dynamic shared memory layout (byte offsets), identical on host and device.
+// The pipelined variant adds, per pair of (dynamics, cost) warps, a ring of
+// kRing slots of states (5 float4: state, compensation terms, input cost)
+// and four mbarriers per slot (two used: state full / state empty).
+constexpr int kRing = 4;
+
 struct SmemLayout {
-    unsigned obs, ref, u, S, e, list, part, wlist, total;
+    unsigned obs, ref, u, S, e, list, part, wlist, uring, iring, xring, bars, total;
 };
 
 __host__ __device__ inline unsigned align_up(unsigned v, unsigned a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int block, int lanes) {
+__host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int block, int lanes, bool pipe) {
     SmemLayout L;
-    const int spb = block / lanes;
+    const int spb = pipe ? block / (1 + lanes) : block / lanes;
     const int npart = block > N_max ? block : N_max;
+    const unsigned slots = pipe ? (unsigned)(spb / 32) * kRing * 32u : 0u;
     unsigned o = 0;
     L.obs = o;  o = align_up(o + 16u * (unsigned)M_max, 128);
     L.ref = o;  o = align_up(o + 64u * (unsigned)(N_max + 1), 128);
@@ -425,6 +447,10 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.list = o; o = align_up(o + 4u * (unsigned)spb, 128);
     L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
     L.wlist = o; o = align_up(o + 8u * (unsigned)block, 128);
+    L.uring = o;
+    L.iring = o;
+    L.xring = o; o = align_up(o + 80u * slots, 128);
+    L.bars = o;  o = align_up(o + 8u * 4u * (slots / 32u), 128);
     L.total = o;
     return L;
 }
@@ -435,12 +461,12 @@ constexpr float kMaxExpArg = 104.0f;
 
 // --------------------------------------------------------------- the kernel
 
-template <int LANES>
+template <int LANES, bool PIPE>
 __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ DevInstance sI;
-    __shared__ int s_tile, s_inst, s_tile_in_inst, s_last, s_count;
+    __shared__ int s_tile, s_inst, s_tile_in_inst, s_last, s_count, s_abort;
     __shared__ float s_x0[16], s_xhat[13], s_eta;
     __shared__ double s_rho;
     __shared__ double s_redd[32];
@@ -448,12 +474,15 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
 
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
-    const int spb = nthreads / LANES;
-    const int group = tid / LANES;
-    const int lane = tid % LANES;
+    // PIPE: samples [0, spb) have a dynamics thread (tid < spb) and LANES
+    // cost lanes (tid >= spb) in separate warps; otherwise LANES lanes per
+    // sample.
+    const int spb = PIPE ? nthreads / (1 + LANES) : nthreads / LANES;
+    const int group = PIPE ? (tid < spb ? tid : (tid - spb) / LANES) : tid / LANES;
+    const int lane = PIPE ? (tid < spb ? 0 : (tid - spb) % LANES) : tid % LANES;
     const int warp = tid >> 5, wlane = tid & 31, nwarps = nthreads >> 5;
 
-    const SmemLayout L = smem_layout(a.N_max, a.M_max, nthreads, LANES);
+    const SmemLayout L = smem_layout(a.N_max, a.M_max, nthreads, LANES, PIPE);
     float4* sobs = reinterpret_cast<float4*>(smem + L.obs);
     float4* sref = reinterpret_cast<float4*>(smem + L.ref);
     float4* su = reinterpret_cast<float4*>(smem + L.u);
@@ -465,8 +494,15 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
 
     const unsigned bar = smem_addr(&mbar);
     unsigned phase = 0;
-    if (tid == 0) mbar_init(bar, 1);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        s_abort = 0;
+        if (PIPE)  // per (pair, slot): [2] state full (dynamics warp), [3] state empty (cost lanes)
+            for (int b = 0; b < (spb / 32) * kRing * 4; ++b)
+                mbar_init(smem_addr(smem + L.bars) + 8u * b, (b & 3) == 3 ? 32 * LANES : 32);
+    }
     __syncthreads();
+    unsigned g_run = 0;  // pipeline steps run so far by this block (ring slot / phase)
 
     const DevModel& Mdl = a.M;
     const DevCost& C = a.C;
@@ -487,7 +523,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
             }
         }
         __syncthreads();
-        if (s_tile >= n_tiles) break;
+        if (s_tile >= n_tiles || s_abort) break;
         const int inst = s_inst;
         const int tile = s_tile_in_inst;
         const int K = sI.K, N = sI.N, M = sI.M;
@@ -549,58 +585,162 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
         __syncthreads();
 
         // --------------------------------------------------- rollouts
-        const int k_raw = tile * spb + group;
-        const bool valid = k_raw < K;
-        const unsigned k = (unsigned)(valid ? k_raw : K - 1);
-        State x;
-        x.px = s_x0[0]; x.py = s_x0[1]; x.pz = s_x0[2]; x.qw = s_x0[3]; x.qx = s_x0[4];
-        x.qy = s_x0[5]; x.qz = s_x0[6]; x.vx = s_x0[7]; x.vy = s_x0[8]; x.vz = s_x0[9];
-        x.wx = s_x0[10]; x.wy = s_x0[11]; x.wz = s_x0[12];
+        if constexpr (!PIPE) {
+            const int k_raw = tile * spb + group;
+            const bool valid = k_raw < K;
+            const unsigned k = (unsigned)(valid ? k_raw : K - 1);
+            State x;
+            x.px = s_x0[0]; x.py = s_x0[1]; x.pz = s_x0[2]; x.qw = s_x0[3]; x.qx = s_x0[4];
+            x.qy = s_x0[5]; x.qz = s_x0[6]; x.vx = s_x0[7]; x.vy = s_x0[8]; x.vz = s_x0[9];
+            x.wx = s_x0[10]; x.wy = s_x0[11]; x.wz = s_x0[12];
 
-        // S_k = c_obs * (states in collision) + the continuous cost, kept
-        // apart: the indicator is an exact count and the continuous part a
-        // compensated FP32 sum, combined in FP64 only for the weights.
-        Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float S = 0.0f, Sc = 0.0f;
-        int nhit = 0;
-        bool hit = false;
-        unsigned kept = 0;  // obstacles evaluated by this warp (uniform over the warp)
-        kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
-                             obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &hit, &kept));
-        if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
-        nhit += hit ? 1 : 0;
-        float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int j = 0; j < N; ++j) {
-            const float4 d = noise_delta(normals4(k, (unsigned)j, iter, key0, key1), sigma);
-            const float4 un = su[j];
-            const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
-                                                          __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
-            float step = fmaf(C.R[0], u.x * u.x, fmaf(C.R[1], u.y * u.y, fmaf(C.R[2], u.z * u.z, C.R[3] * u.w * u.w)));
-            if (j > 0) {
-                const float ex = u.x - u_prev.x, ey = u.y - u_prev.y, ez = u.z - u_prev.z, ew = u.w - u_prev.w;
-                step += fmaf(C.Rd[0], ex * ex, fmaf(C.Rd[1], ey * ey, fmaf(C.Rd[2], ez * ez, C.Rd[3] * ew * ew)));
-            }
-            u_prev = u;
-            const Feasible f = feasible(Mdl, x, u, inv_dt);
-            rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
-            step += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
-            step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, wlane, wlist,
-                                         &hit, &kept);
-            if (C.grid) hit |= grid_hit(C, (x.px - cmp.px) + p0x, (x.py - cmp.py) + p0y, (x.pz - cmp.pz) + p0z);
+            // S_k = c_obs * (states in collision) + the continuous cost, kept
+            // apart: the indicator is an exact count and the continuous part a
+            // compensated FP32 sum, combined in FP64 only for the weights.
+            Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float S = 0.0f, Sc = 0.0f;
+            int nhit = 0;
+            bool hit = false;
+            unsigned kept = 0;  // obstacles evaluated by this warp (uniform over the warp)
+            kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
+                                 obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &hit, &kept));
+            if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
             nhit += hit ? 1 : 0;
-            kahan_add(S, Sc, step);
+            float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < N; ++j) {
+                const float4 d = noise_delta(normals4(k, (unsigned)j, iter, key0, key1), sigma);
+                const float4 un = su[j];
+                const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
+                                                              __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
+                float step = fmaf(C.R[0], u.x * u.x, fmaf(C.R[1], u.y * u.y, fmaf(C.R[2], u.z * u.z, C.R[3] * u.w * u.w)));
+                if (j > 0) {
+                    const float ex = u.x - u_prev.x, ey = u.y - u_prev.y, ez = u.z - u_prev.z, ew = u.w - u_prev.w;
+                    step += fmaf(C.Rd[0], ex * ex, fmaf(C.Rd[1], ey * ey, fmaf(C.Rd[2], ez * ez, C.Rd[3] * ew * ew)));
+                }
+                u_prev = u;
+                const Feasible f = feasible(Mdl, x, u, inv_dt);
+                rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
+                step += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
+                step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, wlane, wlist,
+                                             &hit, &kept);
+                if (C.grid) hit |= grid_hit(C, (x.px - cmp.px) + p0x, (x.py - cmp.py) + p0y, (x.pz - cmp.pz) + p0z);
+                nhit += hit ? 1 : 0;
+                kahan_add(S, Sc, step);
+            }
+            if (a.stats) {
+                // Evaluated pairs: kept obstacles x valid samples of this warp.
+                const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, valid && lane == 0));
+                if (wlane == 0 && kept) atomicAdd(a.stats, (unsigned long long)kept * nvalid);
+            }
+            if (lane == 0) {
+                const double Sd = (double)C.c_obs * (double)nhit + ((double)S - (double)Sc);
+                if (valid && sI.costs) sI.costs[k_raw] = (float)Sd;
+                sS[group] = (valid && isfinite(Sd)) ? Sd : (double)INFINITY;
+            }
+            __syncthreads();
+        } else {
+            // Pipelined rollout.  The dynamics thread of a sample draws the
+            // noise (one step ahead, overlapping the RK4 chain), clamps the
+            // control, forms the input cost and runs the constraint pipeline
+            // and RK4; it hands each new state (with its compensation terms
+            // and the step's input cost) to the sample's cost thread through
+            // a ring in shared memory.  The cost thread scores the states
+            // (tracking, obstacles, grid) while the dynamics thread is
+            // already integrating the next steps.  Every wait is bounded.
+            const bool is_cost = tid >= spb;
+            const int pw = group >> 5;  // warp pair
+            float4* xring = reinterpret_cast<float4*>(smem + L.xring);
+            const unsigned bars = smem_addr(smem + L.bars);
+            volatile int* abort_flag = &s_abort;
+            auto slot_of = [&](unsigned g) { return (int)(g % kRing); };
+            auto bar_of = [&](int slot, int kind) { return bars + 8u * (unsigned)((pw * kRing + slot) * 4 + kind); };
+            auto ring_idx = [&](int slot) { return (pw * kRing + slot) * 32 + (group & 31); };
+            constexpr int X_FULL = 2, X_EMPTY = 3;
+            const int k_raw = tile * spb + group;
+            const bool valid = k_raw < K;
+            const unsigned k = (unsigned)(valid ? k_raw : K - 1);
+            State x;
+            x.px = s_x0[0]; x.py = s_x0[1]; x.pz = s_x0[2]; x.qw = s_x0[3]; x.qx = s_x0[4];
+            x.qy = s_x0[5]; x.qz = s_x0[6]; x.vx = s_x0[7]; x.vy = s_x0[8]; x.vz = s_x0[9];
+            x.wx = s_x0[10]; x.wy = s_x0[11]; x.wz = s_x0[12];
+            Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (!is_cost) {
+                float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 d_next = noise_delta(normals4(k, 0u, iter, key0, key1), sigma);
+                for (int j = 0; j < N; ++j) {
+                    const unsigned g = g_run + (unsigned)j;
+                    const int slot = slot_of(g);
+                    const unsigned ph = (g / kRing) & 1u;
+                    const float4 d = d_next;
+                    d_next = noise_delta(normals4(k, (unsigned)min(j + 1, N - 1), iter, key0, key1), sigma);
+                    const float4 un = su[j];
+                    const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
+                                                                  __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
+                    float ucost = fmaf(C.R[0], u.x * u.x,
+                                       fmaf(C.R[1], u.y * u.y, fmaf(C.R[2], u.z * u.z, C.R[3] * u.w * u.w)));
+                    if (j > 0) {
+                        const float ex = u.x - u_prev.x, ey = u.y - u_prev.y, ez = u.z - u_prev.z,
+                                    ew = u.w - u_prev.w;
+                        ucost += fmaf(C.Rd[0], ex * ex, fmaf(C.Rd[1], ey * ey, fmaf(C.Rd[2], ez * ez, C.Rd[3] * ew * ew)));
+                    }
+                    u_prev = u;
+                    const Feasible f = feasible(Mdl, x, u, inv_dt);
+                    rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
+                    if (g >= (unsigned)kRing) mbar_wait_or_abort(bar_of(slot, X_EMPTY), ph ^ 1u, abort_flag);
+                    float4* xs = xring + 5 * ring_idx(slot);
+                    xs[0] = make_float4(x.px, x.py, x.pz, x.qw);
+                    xs[1] = make_float4(x.qx, x.qy, x.qz, x.vx);
+                    xs[2] = make_float4(x.vy, x.vz, x.wx, x.wy);
+                    xs[3] = make_float4(x.wz, cmp.px, cmp.py, cmp.pz);
+                    xs[4] = make_float4(cmp.vx, cmp.vy, cmp.vz, ucost);
+                    mbar_arrive(bar_of(slot, X_FULL));
+                }
+            } else {
+                float S = 0.0f, Sc = 0.0f;
+                int nhit = 0;
+                bool hit = false;
+                unsigned kept = 0;
+                kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
+                                     obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &hit, &kept));
+                if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
+                nhit += hit ? 1 : 0;
+                for (int j = 0; j < N; ++j) {
+                    const unsigned g = g_run + (unsigned)j;
+                    const int slot = slot_of(g);
+                    const unsigned ph = (g / kRing) & 1u;
+                    State xs;
+                    Comp cs;
+                    const bool ok = mbar_wait_or_abort(bar_of(slot, X_FULL), ph, abort_flag);
+                    const float4* xr = xring + 5 * ring_idx(slot);
+                    const float4 a0 = xr[0], a1 = xr[1], a2 = xr[2], a3 = xr[3], a4 = xr[4];
+                    mbar_arrive(bar_of(slot, X_EMPTY));
+                    xs.px = a0.x; xs.py = a0.y; xs.pz = a0.z; xs.qw = a0.w; xs.qx = a1.x; xs.qy = a1.y;
+                    xs.qz = a1.z; xs.vx = a1.w; xs.vy = a2.x; xs.vz = a2.y; xs.wx = a2.z; xs.wy = a2.w;
+                    xs.wz = a3.x;
+                    cs.px = a3.y; cs.py = a3.z; cs.pz = a3.w; cs.vx = a4.x; cs.vy = a4.y; cs.vz = a4.z;
+                    float step = ok ? a4.w : NAN;
+                    step += tracking_cost(C, xs, cs, &sref[4 * (j + 1)]);
+                    step += obstacle_cost<LANES>(C, xs.px - cs.px, xs.py - cs.py, xs.pz - cs.pz, sobs, M, lane, wlane,
+                                                 wlist, &hit, &kept);
+                    if (C.grid)
+                        hit |= grid_hit(C, (xs.px - cs.px) + p0x, (xs.py - cs.py) + p0y, (xs.pz - cs.pz) + p0z);
+                    nhit += hit ? 1 : 0;
+                    kahan_add(S, Sc, step);
+                }
+                if (a.stats) {
+                    const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, valid && lane == 0));
+                    if (wlane == 0 && kept) atomicAdd(a.stats, (unsigned long long)kept * nvalid);
+                }
+                if (lane == 0) {  // the cost lanes of a sample hold bitwise identical sums
+                    const double Sd = (double)C.c_obs * (double)nhit + ((double)S - (double)Sc);
+                    if (valid && sI.costs) sI.costs[k_raw] = (float)Sd;
+                    sS[group] = (valid && isfinite(Sd)) ? Sd : (double)INFINITY;
+                }
+            }
+            g_run += (unsigned)N;
+            __syncthreads();
+            if (s_abort && tid == 0) atomicOr(&a.errflags[inst], ERR_TIMEOUT);
         }
-        if (a.stats) {
-            // Evaluated pairs: kept obstacles x valid samples of this warp.
-            const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, valid && lane == 0));
-            if (wlane == 0 && kept) atomicAdd(a.stats, (unsigned long long)kept * nvalid);
-        }
-        if (lane == 0) {
-            const double Sd = (double)C.c_obs * (double)nhit + ((double)S - (double)Sc);
-            if (valid && sI.costs) sI.costs[k_raw] = (float)Sd;
-            sS[group] = (valid && isfinite(Sd)) ? Sd : (double)INFINITY;
-        }
-        __syncthreads();
 
         // ------------------------------------- tile min, weights, eta_t
         if (warp == 0) {
@@ -789,71 +929,83 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
 // ------------------------------------------------------------------- host
 
 bool shape_supported(Shape s) {
+    if (s.pipe == 1) {
+        // A dynamics warp plus `lanes` cost warps per 32 samples.
+        const int unit = 32 * (1 + s.lanes);
+        return (s.lanes == 1 || s.lanes == 2) && s.block >= unit && s.block <= 512 && s.block % unit == 0;
+    }
     const bool lanes_ok = s.lanes == 1 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8;
     const bool block_ok = s.block == 64 || s.block == 128 || s.block == 256 || s.block == 512;
-    return lanes_ok && block_ok;
+    return s.pipe == 0 && lanes_ok && block_ok;
 }
 
 size_t smem_bytes(int N_max, int M_max, Shape s) {
-    return smem_layout(N_max, M_max, s.block, s.lanes).total;
+    return smem_layout(N_max, M_max, s.block, s.lanes, s.pipe != 0).total;
 }
 
 // Largest dynamic shared memory opted in so far, per instantiation.  The
 // attribute is raised only when a launch needs more, so launches that are
 // being captured into a graph (after a first, uncaptured preparation) make
 // no attribute call.
-template <int LANES>
+template <int LANES, bool PIPE>
 static std::atomic<int>& smem_opt_in() {
     static std::atomic<int> v{0};
     return v;
 }
 
-template <int LANES>
+template <int LANES, bool PIPE>
 static cudaError_t prepare_t(size_t smem) {
-    if ((int)smem <= smem_opt_in<LANES>().load()) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(mppi_step_kernel<LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((int)smem <= smem_opt_in<LANES, PIPE>().load()) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(mppi_step_kernel<LANES, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess) {
-        int cur = smem_opt_in<LANES>().load();
-        while ((int)smem > cur && !smem_opt_in<LANES>().compare_exchange_weak(cur, (int)smem)) {
+        int cur = smem_opt_in<LANES, PIPE>().load();
+        while ((int)smem > cur && !smem_opt_in<LANES, PIPE>().compare_exchange_weak(cur, (int)smem)) {
         }
     }
     return e;
 }
 
-template <int LANES>
+template <int LANES, bool PIPE>
 static cudaError_t launch_t(const LaunchArgs& a, int block, int grid, size_t smem, cudaStream_t st) {
-    cudaError_t e = prepare_t<LANES>(smem);
+    cudaError_t e = prepare_t<LANES, PIPE>(smem);
     if (e != cudaSuccess) return e;
-    mppi_step_kernel<LANES><<<grid, block, smem, st>>>(a);
+    mppi_step_kernel<LANES, PIPE><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tiles(const LaunchArgs& a, Shape s, int grid, size_t smem, cudaStream_t st) {
+    if (s.pipe) {
+        if (s.lanes == 1) return launch_t<1, true>(a, s.block, grid, smem, st);
+        if (s.lanes == 2) return launch_t<2, true>(a, s.block, grid, smem, st);
+        return cudaErrorInvalidValue;
+    }
     switch (s.lanes) {
-        case 1: return launch_t<1>(a, s.block, grid, smem, st);
-        case 2: return launch_t<2>(a, s.block, grid, smem, st);
-        case 4: return launch_t<4>(a, s.block, grid, smem, st);
-        case 8: return launch_t<8>(a, s.block, grid, smem, st);
+        case 1: return launch_t<1, false>(a, s.block, grid, smem, st);
+        case 2: return launch_t<2, false>(a, s.block, grid, smem, st);
+        case 4: return launch_t<4, false>(a, s.block, grid, smem, st);
+        case 8: return launch_t<8, false>(a, s.block, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int LANES>
+template <int LANES, bool PIPE>
 static int occupancy_t(int block, size_t smem) {
     int n = 0;
-    prepare_t<LANES>(smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mppi_step_kernel<LANES>, block, smem) != cudaSuccess)
+    prepare_t<LANES, PIPE>(smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mppi_step_kernel<LANES, PIPE>, block, smem) !=
+        cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
 int max_active_blocks(Shape s, size_t smem) {
+    if (s.pipe) return s.lanes == 2 ? occupancy_t<2, true>(s.block, smem) : occupancy_t<1, true>(s.block, smem);
     switch (s.lanes) {
-        case 1: return occupancy_t<1>(s.block, smem);
-        case 2: return occupancy_t<2>(s.block, smem);
-        case 4: return occupancy_t<4>(s.block, smem);
-        case 8: return occupancy_t<8>(s.block, smem);
+        case 1: return occupancy_t<1, false>(s.block, smem);
+        case 2: return occupancy_t<2, false>(s.block, smem);
+        case 4: return occupancy_t<4, false>(s.block, smem);
+        case 8: return occupancy_t<8, false>(s.block, smem);
         default: return 1;
     }
 }

@@ -299,7 +299,7 @@ int mppi_server_create(const mppi_model* model, const mppi_params* params, const
         c.N_max > MPPI_N_MAX || c.M_max < 0 || c.M_max > MPPI_M_MAX || c.queue_capacity < 1 ||
         c.max_batch_samples < 1 || c.hbm_budget_bytes < 1)
         return MPPI_EINVAL;
-    if ((c.block || c.lanes) && !mppi::shape_supported(mppi::Shape{c.block, c.lanes})) return MPPI_EINVAL;
+    if ((c.block || c.lanes) && !mppi::shape_supported(mppi::Shape{c.block, c.lanes, 0})) return MPPI_EINVAL;
     const int64_t reserve = (int64_t)c.slots * slot_bytes(c);
     if (reserve > c.hbm_budget_bytes) return MPPI_ENOMEM;
 
@@ -324,7 +324,7 @@ int mppi_server_create(const mppi_model* model, const mppi_params* params, const
         p.N = c.N_max;
         if ((rc = mppi_create(model, &p, &cap, &slot.h))) break;
         if (c.block || c.lanes) {
-            mppi_shape sh{c.block, c.lanes};
+            mppi_shape sh{c.block, c.lanes, 0};
             mppi_set_shape(slot.h, &sh);
         }
         slot.in_floats = in_floats;

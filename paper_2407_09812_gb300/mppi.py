@@ -55,7 +55,7 @@ class Instance(C.Structure):
 
 
 class Shape(C.Structure):
-    _fields_ = [("block", C.c_int32), ("lanes", C.c_int32)]
+    _fields_ = [("block", C.c_int32), ("lanes", C.c_int32), ("pipelined", C.c_int32)]
 
 
 class ServerCfg(C.Structure):
@@ -280,19 +280,19 @@ class Solver:
         _check(fn(self.h, arr, len(instances), _stream_ptr(stream)), "mppi_solve_batch")
 
     # ---------------------------------------------------------- launch shape
-    def set_shape(self, block: int = 0, lanes: int = 0):
-        s = Shape(block, lanes)
+    def set_shape(self, block: int = 0, lanes: int = 0, pipelined: int = 0):
+        s = Shape(block, lanes, pipelined)
         _check(lib().mppi_set_shape(self.h, C.byref(s)), "mppi_set_shape")
 
     def get_shape(self, K: int, N: int, M: int):
         s = Shape()
         _check(lib().mppi_get_shape(self.h, K, N, M, C.byref(s)), "mppi_get_shape")
-        return s.block, s.lanes
+        return s.block, s.lanes, s.pipelined
 
     def autotune(self, K: int, N: int, M: int, stream=None):
         s = Shape()
         _check(lib().mppi_autotune(self.h, K, N, M, C.byref(s), _stream_ptr(stream)), "mppi_autotune")
-        return s.block, s.lanes
+        return s.block, s.lanes, s.pipelined
 
 
 def solve_noalloc(model: dict, params: dict, x_hat, ref, obstacles, u_nom, it: int, u_out=None, u_cmd=None,

@@ -54,19 +54,19 @@ def _cap(probs):
             "N_max": max(p["params"]["N"] for p in probs), "M_max": 64}
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_batch_matches_oracle_and_alone(M, orc, inp, graph):
+@pytest.mark.parametrize("graph,shape", [(False, (128, 2, 0)), (True, (128, 2, 0)), (True, (256, 1, 1))])
+def test_batch_matches_oracle_and_alone(M, orc, inp, graph, shape):
     import torch
     probs = _uneven(inp)
     s = M.Solver(probs[0]["model"], probs[0]["params"], _cap(probs))
-    s.set_shape(128, 2)
+    s.set_shape(*shape)
     insts = [_device(p, torch) for p in probs]
     s.solve_batch(insts, graph=graph)
     torch.cuda.synchronize()
     batched = [_host(d) for d in insts]
     # Alone, same launch shape.
     alone_solver = M.Solver(probs[0]["model"], probs[0]["params"], _cap(probs))
-    alone_solver.set_shape(128, 2)
+    alone_solver.set_shape(*shape)
     for p, b in zip(probs, batched):
         alone_solver.set_params(p["params"])
         d = _device(p, torch)
@@ -133,6 +133,7 @@ def test_autotuner_picks_a_supported_shape_and_uses_it(M, orc, inp):
     before = s.get_shape(3000, 30, 48)
     best = s.autotune(3000, 30, 48)
     assert best[0] in (64, 128, 256, 512) and best[1] in (1, 2, 4, 8) and best[0] // best[1] >= 8
+    assert best[2] in (0, 1) and (best[2] == 0 or best[1] == 1)
     assert s.get_shape(3000, 30, 48) == best
     assert s.get_shape(3000, 30, 0) == s.get_shape(3000, 30, 0)  # other buckets keep their default
     out = s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"], want_costs=True)

@@ -129,13 +129,32 @@ def test_nonfinite_state_reports_and_keeps_nominal(M, inp):
 def test_every_launch_shape_matches_and_is_deterministic(M, orc, inp):
     prob = inp.eight_with_spheres(K=3000, N=20, M=40, t0=3.0, **{"lambda": 500.0})
     ref = orc.mppi_step(prob, n_threads=8)
-    for block in (64, 128, 256, 512):
-        for lanes in (1, 2, 4, 8):
-            a = gpu_solve(M, prob, shape=(block, lanes))
+    shapes = [(b, l, 0) for b in (64, 128, 256, 512) for l in (1, 2, 4, 8)]
+    shapes += [(128, 1, 1), (256, 1, 1), (512, 1, 1), (96, 2, 1), (192, 2, 1), (384, 2, 1)]
+    for block, lanes, pipe in shapes:
+        if True:
+            a = gpu_solve(M, prob, shape=(block, lanes, pipe))
             assert_step_close(prob, a, ref)
-            b = gpu_solve(M, prob, shape=(block, lanes))
+            b = gpu_solve(M, prob, shape=(block, lanes, pipe))
             for k in ("u_out", "costs", "u_cmd"):
-                assert np.array_equal(a[k], b[k]), (block, lanes, k)
+                assert np.array_equal(a[k], b[k]), (block, lanes, pipe, k)
+
+
+@pytest.mark.parametrize("K,N,Mo", [(16384, 100, 64), (1000, 1, 3), (257, 7, 0), (3000, 37, 40)])
+def test_pipelined_form_matches_one_thread_per_sample(M, orc, inp, K, N, Mo):
+    """The pipelined form (dynamics and cost threads per sample, handing
+    states over through mbarrier-guarded rings) gives the per-sample costs
+    of one thread per sample to FP32 rounding (the same arithmetic compiled
+    in two places) and matches the oracle."""
+    prob = inp.eight_with_spheres(K=K, N=N, M=Mo, t0=0.6, **{"lambda": 200.0})
+    if Mo == 0:
+        prob["obstacles"] = np.zeros((0, 4), np.float32)
+    b = gpu_solve(M, prob, shape=(128, 1, 0))
+    ref = orc.mppi_step(prob, n_threads=16)
+    for shape in ((256, 1, 1), (384, 2, 1)):
+        a = gpu_solve(M, prob, shape=shape)
+        assert cost_err(a["costs"], b["costs"])[0] <= 1e-6
+        assert_step_close(prob, a, ref)
 
 
 def test_closed_loop_full_size(M, orc, inp):
