@@ -423,8 +423,8 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Dynamic shared memory layout (byte offsets), identical on host and device.
 // The pipelined variant adds, per pair of (dynamics, cost) warps, a ring of
-// kRing slots of states (5 float4: state, compensation terms, input cost)
-// and four mbarriers per slot (two used: state full / state empty).
+// kRing slots (2 float4: position, its compensation, and the step's input
+// and tracking cost) and four mbarriers per slot (two used: full / empty).
 constexpr int kRing = 4;
 
 struct SmemLayout {
@@ -449,7 +449,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.wlist = o; o = align_up(o + 8u * (unsigned)block, 128);
     L.uring = o;
     L.iring = o;
-    L.xring = o; o = align_up(o + 80u * slots, 128);
+    L.xring = o; o = align_up(o + 32u * slots, 128);
     L.bars = o;  o = align_up(o + 8u * 4u * (slots / 32u), 128);
     L.total = o;
     return L;
@@ -641,12 +641,13 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
         } else {
             // Pipelined rollout.  The dynamics thread of a sample draws the
             // noise (one step ahead, overlapping the RK4 chain), clamps the
-            // control, forms the input cost and runs the constraint pipeline
-            // and RK4; it hands each new state (with its compensation terms
-            // and the step's input cost) to the sample's cost thread through
-            // a ring in shared memory.  The cost thread scores the states
-            // (tracking, obstacles, grid) while the dynamics thread is
-            // already integrating the next steps.  Every wait is bounded.
+            // control, runs the constraint pipeline and RK4 and forms the
+            // step's input, input-change and tracking cost; it hands the new
+            // position (with its compensation terms) and that cost to the
+            // sample's cost lanes through a ring in shared memory.  The cost
+            // lanes score the positions against the obstacles and the grid
+            // while the dynamics thread is already integrating the next
+            // steps.  Every wait is bounded.
             const bool is_cost = tid >= spb;
             const int pw = group >> 5;  // warp pair
             float4* xring = reinterpret_cast<float4*>(smem + L.xring);
@@ -686,13 +687,13 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                     u_prev = u;
                     const Feasible f = feasible(Mdl, x, u, inv_dt);
                     rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
+                    // Input, input-change and tracking cost of the step, in
+                    // the same order as the one-thread form.
+                    ucost += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
                     if (g >= (unsigned)kRing) mbar_wait_or_abort(bar_of(slot, X_EMPTY), ph ^ 1u, abort_flag);
-                    float4* xs = xring + 5 * ring_idx(slot);
-                    xs[0] = make_float4(x.px, x.py, x.pz, x.qw);
-                    xs[1] = make_float4(x.qx, x.qy, x.qz, x.vx);
-                    xs[2] = make_float4(x.vy, x.vz, x.wx, x.wy);
-                    xs[3] = make_float4(x.wz, cmp.px, cmp.py, cmp.pz);
-                    xs[4] = make_float4(cmp.vx, cmp.vy, cmp.vz, ucost);
+                    float4* xs = xring + 2 * ring_idx(slot);
+                    xs[0] = make_float4(x.px, x.py, x.pz, ucost);
+                    xs[1] = make_float4(cmp.px, cmp.py, cmp.pz, 0.0f);
                     mbar_arrive(bar_of(slot, X_FULL));
                 }
             } else {
@@ -708,22 +709,14 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                     const unsigned g = g_run + (unsigned)j;
                     const int slot = slot_of(g);
                     const unsigned ph = (g / kRing) & 1u;
-                    State xs;
-                    Comp cs;
                     const bool ok = mbar_wait_or_abort(bar_of(slot, X_FULL), ph, abort_flag);
-                    const float4* xr = xring + 5 * ring_idx(slot);
-                    const float4 a0 = xr[0], a1 = xr[1], a2 = xr[2], a3 = xr[3], a4 = xr[4];
+                    const float4* xr = xring + 2 * ring_idx(slot);
+                    const float4 a0 = xr[0], a1 = xr[1];
                     mbar_arrive(bar_of(slot, X_EMPTY));
-                    xs.px = a0.x; xs.py = a0.y; xs.pz = a0.z; xs.qw = a0.w; xs.qx = a1.x; xs.qy = a1.y;
-                    xs.qz = a1.z; xs.vx = a1.w; xs.vy = a2.x; xs.vz = a2.y; xs.wx = a2.z; xs.wy = a2.w;
-                    xs.wz = a3.x;
-                    cs.px = a3.y; cs.py = a3.z; cs.pz = a3.w; cs.vx = a4.x; cs.vy = a4.y; cs.vz = a4.z;
-                    float step = ok ? a4.w : NAN;
-                    step += tracking_cost(C, xs, cs, &sref[4 * (j + 1)]);
-                    step += obstacle_cost<LANES>(C, xs.px - cs.px, xs.py - cs.py, xs.pz - cs.pz, sobs, M, lane, wlane,
-                                                 wlist, &hit, &kept);
-                    if (C.grid)
-                        hit |= grid_hit(C, (xs.px - cs.px) + p0x, (xs.py - cs.py) + p0y, (xs.pz - cs.pz) + p0z);
+                    const float qpx = a0.x - a1.x, qpy = a0.y - a1.y, qpz = a0.z - a1.z;  // compensated position
+                    float step = ok ? a0.w : NAN;
+                    step += obstacle_cost<LANES>(C, qpx, qpy, qpz, sobs, M, lane, wlane, wlist, &hit, &kept);
+                    if (C.grid) hit |= grid_hit(C, qpx + p0x, qpy + p0y, qpz + p0z);
                     nhit += hit ? 1 : 0;
                     kahan_add(S, Sc, step);
                 }
