@@ -243,3 +243,16 @@ def test_evaluated_pair_counter(M, orc, inp):
         else:
             assert 0 < n < total
         assert_step_close(p, g, orc.mppi_step(p, n_threads=8))
+
+
+def test_paper_operating_point(M, orc, inp):
+    """Table II: K=896, N=15, dt=0.1 s, lambda=1e-4, Sigma=diag(0.60, 0.15,
+    0.15, 0.05) as a covariance, Table II weights, motor limits."""
+    import math
+    sig = tuple(math.sqrt(v) for v in (0.60, 0.15, 0.15, 0.05))
+    prob = inp.eight_with_spheres(K=896, N=15, dt=0.1, M=0, **{"lambda": 1e-4, "sigma": sig})
+    prob["x_hat"] = prob["x_hat"].copy()
+    prob["x_hat"][0:3] += np.array([0.3, -0.2, 0.1], np.float32)
+    for it in range(3):
+        p = dict(prob, iter=it)
+        assert_step_close(p, gpu_solve(M, p), orc.mppi_step(p, n_threads=8))
