@@ -214,6 +214,17 @@ int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_
  * required.  NULL turns it off.  The counter must be 8-byte aligned. */
 int mppi_set_counters(mppi_handle h, uint64_t* counters);
 
+/* Failure-path hook (the paper has no counterpart).  Every device-side wait
+ * of the kernel (the obstacle staging copy, the pipelined form's state
+ * ring) is a bounded poll of an mbarrier; polls sets that bound for this
+ * handle's later launches (0: the default, about a second of polling).
+ * stall_obstacle_copy != 0 makes the launches skip the staging copy of the
+ * obstacle list, so that its wait runs out without any fault: every
+ * instance with M > 0 then returns MPPI_ETIMEOUT, its outputs unspecified,
+ * and the context stays usable.  Used by tests of the timeout path; keep
+ * both 0 otherwise.  Returns MPPI_EINVAL for a NULL handle or polls < 0. */
+int mppi_set_wait_limit(mppi_handle h, int64_t polls, int32_t stall_obstacle_copy);
+
 /* Launch shape of the rollout kernel. */
 typedef struct {
     int32_t block;          /* threads per block: 64, 128, 256 or 512       */

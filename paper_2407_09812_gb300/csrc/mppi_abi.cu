@@ -175,6 +175,8 @@ struct mppi_ctx {
     float g_inv_voxel = 0;
 
     unsigned long long* stats = nullptr;  // optional evaluated-pair counter (device)
+    long long wait_polls = 0;             // bound of device-side waits (0: default)
+    int stall_obstacle_copy = 0;          // failure-path test hook
 
     Shape forced{0, 0, 0};
     std::map<uint64_t, Shape> table;
@@ -316,6 +318,8 @@ LaunchArgs base_args(mppi_ctx* h, int n_inst) {
     std::memset(&a, 0, sizeof(a));
     a.partials = h->partials;
     a.stats = h->stats;
+    a.wait_polls = h->wait_polls;
+    a.stall_obstacle_copy = h->stall_obstacle_copy;
     a.done = h->counters + 1;
     a.errflags = h->counters + 1 + n_inst;
     a.M = h->dm;
@@ -564,6 +568,14 @@ int mppi_set_counters(mppi_handle h, uint64_t* counters) {
     if (counters && (reinterpret_cast<uintptr_t>(counters) & 7u)) return MPPI_EINVAL;
     h->stats = reinterpret_cast<unsigned long long*>(counters);
     drop_graphs(h);
+    return MPPI_OK;
+}
+
+int mppi_set_wait_limit(mppi_handle h, int64_t polls, int32_t stall_obstacle_copy) {
+    if (!h || polls < 0) return MPPI_EINVAL;
+    h->wait_polls = polls;
+    h->stall_obstacle_copy = stall_obstacle_copy ? 1 : 0;
+    drop_graphs(h);  // captured launches hold the old values
     return MPPI_OK;
 }
 

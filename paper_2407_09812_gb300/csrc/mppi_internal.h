@@ -85,6 +85,8 @@ struct LaunchArgs {
     unsigned* errflags;         // per-instance error bits
     const int* n_tiles_dev;     // device tile count (graph replay); NULL: n_tiles
     unsigned long long* stats;  // optional: [0] += evaluated (state, obstacle) pairs
+    long long wait_polls;       // bound of every device-side wait (polls); 0: default
+    int stall_obstacle_copy;    // test hook: skip the obstacle copy so its wait runs out
     int n_tiles;
     int n_inst;
     int N_max, M_max;           // sizes the dynamic shared memory was laid out for

@@ -378,9 +378,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     return ok != 0u;
 }
 
-// Bounded wait on one phase of the barrier: ~seconds at most, then false.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-    for (long long i = 0; i < (1ll << 22); ++i)
+// Default bound of every device-side wait, in polls of the barrier (each
+// poll may suspend for a hardware-defined time): about a second.
+constexpr long long kWaitPolls = 1ll << 22;
+
+// Bounded wait on one phase of the barrier, then false.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, long long polls) {
+    for (long long i = 0; i < polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -388,8 +392,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
 // Bounded wait that also gives up when another warp of the block has
 // flagged an abort; a wait that runs out raises the flag itself, so a
 // stuck pipeline drains quickly instead of every later wait timing out.
-__device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity, volatile int* abort_flag) {
-    for (long long i = 0; i < (1ll << 22); ++i) {
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity, volatile int* abort_flag,
+                                                   long long polls) {
+    for (long long i = 0; i < polls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 63) == 63 && *abort_flag) return false;
     }
@@ -466,7 +471,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ DevInstance sI;
-    __shared__ int s_tile, s_inst, s_tile_in_inst, s_last, s_count, s_abort;
+    __shared__ int s_tile, s_inst, s_tile_in_inst, s_last, s_count, s_abort, s_lost;
     __shared__ float s_x0[16], s_xhat[13], s_eta;
     __shared__ double s_rho;
     __shared__ double s_redd[32];
@@ -497,6 +502,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
     if (tid == 0) {
         mbar_init(bar, 1);
         s_abort = 0;
+        s_lost = 0;
         if (PIPE)  // per (pair, slot): [2] state full (dynamics warp), [3] state empty (cost lanes)
             for (int b = 0; b < (spb / 32) * kRing * 4; ++b)
                 mbar_init(smem_addr(smem + L.bars) + 8u * b, (b & 3) == 3 ? 32 * LANES : 32);
@@ -507,6 +513,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
     const DevModel& Mdl = a.M;
     const DevCost& C = a.C;
     const int n_tiles = a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles;
+    const long long wait_polls = a.wait_polls > 0 ? a.wait_polls : kWaitPolls;
 
     for (int round = 0;; ++round) {
         // ---------------------------------------------------- pick a tile
@@ -523,7 +530,12 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
             }
         }
         __syncthreads();
-        if (s_tile >= n_tiles || s_abort) break;
+        if (s_tile >= n_tiles) break;
+        // A block whose obstacle copy never landed (s_lost) or whose
+        // pipeline gave up a wait (s_abort) keeps taking tiles, so that every
+        // instance is still merged and given a status, but skips the copy
+        // and flags each instance it touches: its outputs are unspecified.
+        const bool lost = s_lost != 0;
         const int inst = s_inst;
         const int tile = s_tile_in_inst;
         const int K = sI.K, N = sI.N, M = sI.M;
@@ -534,7 +546,9 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
 
         // ---------------------------------- stage inputs in shared memory
         // Obstacles by one bulk TMA copy (overlaps the loads below).
-        if (tid == 0 && M > 0) bulk_load(smem_addr(sobs), sI.obs, 16u * (unsigned)M, bar);
+        if (tid == 0 && M > 0 && !lost && !a.stall_obstacle_copy)
+            bulk_load(smem_addr(sobs), sI.obs, 16u * (unsigned)M, bar);
+        if (tid == 0 && (lost || s_abort)) atomicOr(&a.errflags[inst], ERR_TIMEOUT);
         if (tid < 13) s_xhat[tid] = sI.x_hat[tid];
         __syncthreads();
         // Origin shift to the state estimate's position: translation
@@ -569,11 +583,16 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
             s_x0[10] = x.wx; s_x0[11] = x.wy; s_x0[12] = x.wz;
         }
         if (M > 0) {
-            if (!mbar_wait_bounded(bar, phase)) {
-                if (tid == 0) atomicOr(&a.errflags[inst], ERR_TIMEOUT);
-                mbar_wait_bounded(bar, phase);  // let the copy land before smem is reused
+            if (!lost) {
+                if (!mbar_wait_bounded(bar, phase, wait_polls)) {
+                    // The copy did not land in time: flag the instance and
+                    // give it one more bounded wait to land before shared
+                    // memory is reused; after that the barrier is given up.
+                    if (tid == 0) atomicOr(&a.errflags[inst], ERR_TIMEOUT);
+                    if (!mbar_wait_bounded(bar, phase, wait_polls)) s_lost = 1;
+                }
+                phase ^= 1u;
             }
-            phase ^= 1u;
             for (int o = tid; o < M; o += nthreads) {
                 const float4 ob = sobs[o];
                 const float reach = fabsf(ob.w) + C.r_uav;
@@ -690,7 +709,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                     // Input, input-change and tracking cost of the step, in
                     // the same order as the one-thread form.
                     ucost += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
-                    if (g >= (unsigned)kRing) mbar_wait_or_abort(bar_of(slot, X_EMPTY), ph ^ 1u, abort_flag);
+                    if (g >= (unsigned)kRing) mbar_wait_or_abort(bar_of(slot, X_EMPTY), ph ^ 1u, abort_flag, wait_polls);
                     float4* xs = xring + 2 * ring_idx(slot);
                     xs[0] = make_float4(x.px, x.py, x.pz, ucost);
                     xs[1] = make_float4(cmp.px, cmp.py, cmp.pz, 0.0f);
@@ -709,7 +728,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                     const unsigned g = g_run + (unsigned)j;
                     const int slot = slot_of(g);
                     const unsigned ph = (g / kRing) & 1u;
-                    const bool ok = mbar_wait_or_abort(bar_of(slot, X_FULL), ph, abort_flag);
+                    const bool ok = mbar_wait_or_abort(bar_of(slot, X_FULL), ph, abort_flag, wait_polls);
                     const float4* xr = xring + 2 * ring_idx(slot);
                     const float4 a0 = xr[0], a1 = xr[1];
                     mbar_arrive(bar_of(slot, X_EMPTY));

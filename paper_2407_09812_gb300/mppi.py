@@ -98,6 +98,7 @@ def lib():
     L.mppi_set_params.argtypes = [_VP, C.POINTER(Params)]
     L.mppi_set_grid.argtypes = [_VP, _VP, C.c_int32, C.c_int32, C.c_int32, _FP, C.c_float]
     L.mppi_set_counters.argtypes = [_VP, _VP]
+    L.mppi_set_wait_limit.argtypes = [_VP, C.c_int64, C.c_int32]
     L.mppi_solve.argtypes = [_VP, _FP, _FP, _FP, C.c_int32, _FP, C.c_uint64, _FP, _FP, _FP, _FP, _FP]
     L.mppi_solve_async.argtypes = [_VP, _VP, _VP, _VP, C.c_int32, _VP, C.c_uint64, _VP, _VP, _VP, _VP, _VP, _VP,
                                    _VP]
@@ -227,6 +228,12 @@ class Solver:
         self._counters = counters
         _check(lib().mppi_set_counters(self.h, None if counters is None else C.c_void_p(counters.data_ptr())),
                "mppi_set_counters")
+
+    def set_wait_limit(self, polls: int = 0, stall_obstacle_copy: bool = False):
+        """mppi_set_wait_limit: bound of the kernel's device-side waits (0:
+        default) and the failure-path hook that skips the obstacle copy."""
+        _check(lib().mppi_set_wait_limit(self.h, int(polls), 1 if stall_obstacle_copy else 0),
+               "mppi_set_wait_limit")
 
     # ---------------------------------------------------------- host buffers
     def solve(self, x_hat, ref, obstacles, u_nom, it: int, want_costs: bool = False) -> dict:

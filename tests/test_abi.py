@@ -67,6 +67,7 @@ def test_host_validation_rejects_bad_arguments(built):
     assert L.mppi_create(None, None, None, C.byref(h)) == mppi.EINVAL
     assert L.mppi_solve(None, None, None, None, 0, None, 0, None, None, None, None, None) == mppi.EINVAL
     assert L.mppi_solve_batch(None, None, 0, None) == mppi.EINVAL
+    assert L.mppi_set_wait_limit(None, 0, 0) == mppi.EINVAL
     assert mppi.strerror(mppi.ENONFINITE) == "every rollout cost was non-finite"
 
 
