@@ -269,7 +269,7 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 // results on all lanes of the sample).
 template <int LANES>
 __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float py, float pz, const float4* so,
-                                               int M, int lane, int wlane, int* wlist, bool* hit_out,
+                                               int M, int lane, int wlane, float4* wob, bool* hit_out,
                                                unsigned* kept_out) {
     float bar = 0.0f;
     bool hit = false;
@@ -281,9 +281,8 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
         const float hiy = key_float(__reduce_max_sync(0xffffffffu, ky));
         const float loz = key_float(__reduce_min_sync(0xffffffffu, kz));
         const float hiz = key_float(__reduce_max_sync(0xffffffffu, kz));
-        auto keep_test = [&](int o) -> bool {
+        auto keep_test = [&](int o, const float4 ob) -> bool {
             if (o >= M) return false;
-            const float4 ob = so[o];
             const float ex = fmaxf(fmaxf(lox - ob.x, ob.x - hix), 0.0f);
             const float ey = fmaxf(fmaxf(loy - ob.y, ob.y - hiy), 0.0f);
             const float ez = ob.w >= 0.0f ? fmaxf(fmaxf(loz - ob.z, ob.z - hiz), 0.0f) : 0.0f;
@@ -297,22 +296,36 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
             hit |= (sg <= 0.0f);
             return ex2_ftz(-C.beta_log2e * fmaxf(sg, 0.0f));
         };
-        // Two 32-obstacle chunks are tested at once; the kept indices go to
-        // the warp's list in ascending order and are then processed by a
-        // counted loop (every lane of a sample takes every LANES-th one).
+        // Two 32-obstacle chunks are tested at once; the kept obstacles are
+        // copied to the warp's list in ascending order and then processed
+        // by a counted loop (every lane of a sample takes every LANES-th
+        // one).
         const unsigned lt = (1u << wlane) - 1u;
         for (int o0 = 0; o0 < M; o0 += 64) {
-            const bool k0 = keep_test(o0 + wlane);
-            const bool k1 = keep_test(o0 + 32 + wlane);
+            const float4 ob0 = o0 + wlane < M ? so[o0 + wlane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 ob1 = o0 + 32 + wlane < M ? so[o0 + 32 + wlane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool k0 = keep_test(o0 + wlane, ob0);
+            const bool k1 = keep_test(o0 + 32 + wlane, ob1);
             const unsigned m0 = __ballot_sync(0xffffffffu, k0);
             const unsigned m1 = __ballot_sync(0xffffffffu, k1);
             const int n0 = __popc(m0);
-            if (k0) wlist[__popc(m0 & lt)] = o0 + wlane;
-            if (k1) wlist[n0 + __popc(m1 & lt)] = o0 + 32 + wlane;
+            if (k0) wob[__popc(m0 & lt)] = ob0;
+            if (k1) wob[n0 + __popc(m1 & lt)] = ob1;
             __syncwarp();
             const int cnt = n0 + __popc(m1);
             *kept_out += (unsigned)cnt;
-            for (int c = lane; c < cnt; c += LANES) bar += term(so[wlist[c]]);
+            // Four terms at a time: their loads and arithmetic are
+            // independent, only the additions stay in list order.
+            int c = lane;
+            for (; c + 3 * LANES < cnt; c += 4 * LANES) {
+                const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
+                const float e0 = term(q0), e1 = term(q1), e2 = term(q2), e3 = term(q3);
+                bar += e0;
+                bar += e1;
+                bar += e2;
+                bar += e3;
+            }
+            for (; c < cnt; c += LANES) bar += term(wob[c]);
             __syncwarp();
         }
     }
@@ -451,7 +464,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.e = o;    o = align_up(o + 4u * (unsigned)spb, 128);
     L.list = o; o = align_up(o + 4u * (unsigned)spb, 128);
     L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
-    L.wlist = o; o = align_up(o + 8u * (unsigned)block, 128);
+    L.wlist = o; o = align_up(o + 32u * (unsigned)block, 128);
     L.uring = o;
     L.iring = o;
     L.xring = o; o = align_up(o + 32u * slots, 128);
@@ -495,7 +508,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
     float* sE = reinterpret_cast<float*>(smem + L.e);
     int* slist = reinterpret_cast<int*>(smem + L.list);
     float4* spart = reinterpret_cast<float4*>(smem + L.part);
-    int* wlist = reinterpret_cast<int*>(smem + L.wlist) + 64 * (threadIdx.x >> 5);
+    float4* wob = reinterpret_cast<float4*>(smem + L.wlist) + 64 * (threadIdx.x >> 5);
 
     const unsigned bar = smem_addr(&mbar);
     unsigned phase = 0;
@@ -622,7 +635,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
             bool hit = false;
             unsigned kept = 0;  // obstacles evaluated by this warp (uniform over the warp)
             kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
-                                 obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &hit, &kept));
+                                 obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, &hit, &kept));
             if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
             nhit += hit ? 1 : 0;
             float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -640,7 +653,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                 const Feasible f = feasible(Mdl, x, u, inv_dt);
                 rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
                 step += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
-                step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, wlane, wlist,
+                step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, wlane, wob,
                                              &hit, &kept);
                 if (C.grid) hit |= grid_hit(C, (x.px - cmp.px) + p0x, (x.py - cmp.py) + p0y, (x.pz - cmp.pz) + p0z);
                 nhit += hit ? 1 : 0;
@@ -721,7 +734,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                 bool hit = false;
                 unsigned kept = 0;
                 kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
-                                     obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wlist, &hit, &kept));
+                                     obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, &hit, &kept));
                 if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
                 nhit += hit ? 1 : 0;
                 for (int j = 0; j < N; ++j) {
@@ -734,7 +747,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                     mbar_arrive(bar_of(slot, X_EMPTY));
                     const float qpx = a0.x - a1.x, qpy = a0.y - a1.y, qpz = a0.z - a1.z;  // compensated position
                     float step = ok ? a0.w : NAN;
-                    step += obstacle_cost<LANES>(C, qpx, qpy, qpz, sobs, M, lane, wlane, wlist, &hit, &kept);
+                    step += obstacle_cost<LANES>(C, qpx, qpy, qpz, sobs, M, lane, wlane, wob, &hit, &kept);
                     if (C.grid) hit |= grid_hit(C, qpx + p0x, qpy + p0y, qpz + p0z);
                     nhit += hit ? 1 : 0;
                     kahan_add(S, Sc, step);
@@ -877,21 +890,70 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
             const float eta = s_eta;
             const bool ok = rho < INFINITY && eta > 0.0f;
             const unsigned errs = a.errflags[inst];
-            // u_out = u_nom + Sigma / eta   (Eq. u_update)
+            // u_out = u_nom + Sigma / eta   (Eq. u_update), Sigma = sum_t
+            // s_t Sigma_t.  The tiles with s_t > 0 are compacted, in
+            // ascending order and a chunk of spb tiles at a time, into shared
+            // memory; threads (j, grp) add the grp-th share of them for step
+            // j (independent loads, so they overlap), and the shares are then
+            // added in group order.
             float* sunew = reinterpret_cast<float*>(su);
-            for (int o = tid; o < 4 * N; o += nthreads) {
-                float acc = 0.0f;
+            const int G = N >= nthreads ? 1 : nthreads / N;
+            for (int w0 = 0; ok && w0 < G * N; w0 += nthreads) {
+                const int w = w0 + tid;
+                const int j = w % N, grp = w / N;
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int t0 = 0; t0 < T; t0 += spb) {
+                    const int ch = min(spb, T - t0);
+                    for (int i = tid; i < ch; i += nthreads) sE[i] = __ldcg(P0 + (long long)(t0 + i) * stride + 3);
+                    __syncthreads();
+                    if (warp == 0) {
+                        int base = 0;
+                        for (int c0 = 0; c0 < ch; c0 += 32) {
+                            const int i = c0 + wlane;
+                            const bool on = i < ch && sE[i] > 0.0f;
+                            const unsigned bal = __ballot_sync(0xffffffffu, on);
+                            if (on) slist[base + __popc(bal & ((1u << wlane) - 1u))] = i;
+                            base += __popc(bal);
+                        }
+                        if (wlane == 0) s_count = base;
+                    }
+                    __syncthreads();
+                    const int cnt = s_count;
+                    if (w < G * N) {
+#pragma unroll 4
+                        for (int ci = grp; ci < cnt; ci += G) {
+                            const int i = slist[ci];
+                            const float st = sE[i];
+                            const float4 v =
+                                __ldcg(reinterpret_cast<const float4*>(P0 + (long long)(t0 + i) * stride + 4) + j);
+                            acc.x = fmaf(st, v.x, acc.x);
+                            acc.y = fmaf(st, v.y, acc.y);
+                            acc.z = fmaf(st, v.z, acc.z);
+                            acc.w = fmaf(st, v.w, acc.w);
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (w < G * N) spart[grp * N + j] = acc;
+            }
+            __syncthreads();
+            for (int j = tid; j < N; j += nthreads) {
+                float4 sg = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (ok) {
-                    for (int t = 0; t < T; ++t) {
-                        const float* Pt = P0 + (long long)t * stride;
-                        const float st = __ldcg(Pt + 3);
-                        if (st > 0.0f) acc = fmaf(st, __ldcg(Pt + 4 + o), acc);
+                    sg = spart[j];
+                    for (int grp = 1; grp < G; ++grp) {
+                        const float4 t = spart[grp * N + j];
+                        sg.x += t.x; sg.y += t.y; sg.z += t.z; sg.w += t.w;
                     }
                 }
-                const float un = sI.u_nom[o];
-                const float v = ok ? un + acc / eta : un;
-                sunew[o] = v;
-                if (sI.u_out) sI.u_out[o] = v;
+                const float acc[4] = {sg.x, sg.y, sg.z, sg.w};
+                for (int c = 0; c < 4; ++c) {
+                    const int o = 4 * j + c;
+                    const float un = sI.u_nom[o];
+                    const float v = ok ? un + acc[c] / eta : un;
+                    sunew[o] = v;
+                    if (sI.u_out) sI.u_out[o] = v;
+                }
             }
             __syncthreads();
             // Warm start: shift by alpha steps with linear interpolation.
