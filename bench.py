@@ -389,7 +389,7 @@ def run_serving(args):
     main = serve.run_fleet(duration_s=args.serve_seconds, n_vehicles=args.serve_vehicles)
     sweep = []
     for nv in (10, 100):
-        r = serve.run_fleet(duration_s=max(1.0, args.serve_seconds / 3), n_vehicles=nv, warmup_s=0.5)
+        r = serve.run_fleet(duration_s=max(1.0, min(10.0, args.serve_seconds / 3)), n_vehicles=nv, warmup_s=0.5)
         sweep.append({k: r[k] for k in ("workload", "solves_per_s", "rollout_steps_per_s", "latency_ms",
                                         "missed_ticks", "ticks", "mean_batch")})
     main["lighter_fleets"] = sweep
@@ -425,7 +425,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-vehicles", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sections")
     ap.add_argument("--section", default="all", choices=["all", "batched", "stress", "serving", "paper"],
