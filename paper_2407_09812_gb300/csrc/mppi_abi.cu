@@ -96,6 +96,7 @@ DevCost make_dev_cost(const mppi_params& p) {
     // ex2.approx.ftz returns exactly 0 below 2^-126: a squared gap beyond
     // 127 / (beta log2 e) contributes nothing (no barrier when beta == 0).
     c.cull = p.beta > 0.0f ? (float)(127.0 / ((double)p.beta * 1.4426950408889634073599)) : INFINITY;
+    c.cull_margin = kCullMargin;
     c.r_uav = p.r_uav;
     c.quat_metric = p.quat_metric; c.tail_mode = p.tail_mode;
     c.shift_alpha = p.shift_alpha; c.delay = p.delay;

@@ -33,11 +33,17 @@ struct DevModel {
 };
 
 // Cost weights and step options shared by every instance of a launch.
+// A warp's kept-obstacle list is built for the warp's position box grown by
+// this margin on every side and reused while all of the warp's positions stay
+// inside; a larger margin means fewer rebuilds but more (exactly zero) terms.
+constexpr float kCullMargin = 1.0f;  // [m]
+
 struct DevCost {
     float c_p, c_q, c_v, c_w;
     float R[4], Rd[4];
     float c_obs, c_bar, beta_log2e, r_uav;
     float cull;             // squared-gap beyond which the barrier is exactly 0 (FP32)
+    float cull_margin;      // enlargement of a warp's box when its kept-obstacle list is built [m]
     int quat_metric, tail_mode;
     float shift_alpha, delay;
     // Occupancy voxel grid (NULL: none): grid[(iz*gy + iy)*gx + ix] != 0 is

@@ -267,28 +267,23 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 // uncut sum.  With LANES lanes per sample the lanes of a sample take every
 // LANES-th kept obstacle and combine by xor-shuffles (bitwise identical
 // results on all lanes of the sample).
+// A warp's kept-obstacle list, kept across steps: exact for every position
+// inside the box [l, h] (the warp's box enlarged by a margin when it was
+// built), so it is reused while all of the warp's positions stay inside.
+// Replicated in every lane.  n = -1: no list yet; -2: a list did not fit
+// (more than 64 kept), lists are not used for the rest of the rollout.
+struct WarpList {
+    float lx, ly, lz, hx, hy, hz;
+    int n;
+};
+
 template <int LANES>
 __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float py, float pz, const float4* so,
-                                               int M, int lane, int wlane, float4* wob, bool* hit_out,
-                                               unsigned* kept_out) {
+                                               int M, int lane, int wlane, float4* wob, WarpList& wl,
+                                               float margin, bool reuse, bool* hit_out, unsigned* kept_out) {
     float bar = 0.0f;
     bool hit = false;
     if (M > 0) {
-        const unsigned kx = float_key(px), ky = float_key(py), kz = float_key(pz);
-        const float lox = key_float(__reduce_min_sync(0xffffffffu, kx));
-        const float hix = key_float(__reduce_max_sync(0xffffffffu, kx));
-        const float loy = key_float(__reduce_min_sync(0xffffffffu, ky));
-        const float hiy = key_float(__reduce_max_sync(0xffffffffu, ky));
-        const float loz = key_float(__reduce_min_sync(0xffffffffu, kz));
-        const float hiz = key_float(__reduce_max_sync(0xffffffffu, kz));
-        auto keep_test = [&](int o, const float4 ob) -> bool {
-            if (o >= M) return false;
-            const float ex = fmaxf(fmaxf(lox - ob.x, ob.x - hix), 0.0f);
-            const float ey = fmaxf(fmaxf(loy - ob.y, ob.y - hiy), 0.0f);
-            const float ez = ob.w >= 0.0f ? fmaxf(fmaxf(loz - ob.z, ob.z - hiz), 0.0f) : 0.0f;
-            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-            return d2 <= (fabsf(ob.w) + C.cull) * 1.0001f;
-        };
         auto term = [&](const float4 ob) {
             const float dx = px - ob.x, dy = py - ob.y, dz = pz - ob.z;
             const float sph = ob.w >= 0.0f ? dz : 0.0f;  // vertical cylinders ignore z
@@ -296,26 +291,9 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
             hit |= (sg <= 0.0f);
             return ex2_ftz(-C.beta_log2e * fmaxf(sg, 0.0f));
         };
-        // Two 32-obstacle chunks are tested at once; the kept obstacles are
-        // copied to the warp's list in ascending order and then processed
-        // by a counted loop (every lane of a sample takes every LANES-th
-        // one).
-        const unsigned lt = (1u << wlane) - 1u;
-        for (int o0 = 0; o0 < M; o0 += 64) {
-            const float4 ob0 = o0 + wlane < M ? so[o0 + wlane] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 ob1 = o0 + 32 + wlane < M ? so[o0 + 32 + wlane] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const bool k0 = keep_test(o0 + wlane, ob0);
-            const bool k1 = keep_test(o0 + 32 + wlane, ob1);
-            const unsigned m0 = __ballot_sync(0xffffffffu, k0);
-            const unsigned m1 = __ballot_sync(0xffffffffu, k1);
-            const int n0 = __popc(m0);
-            if (k0) wob[__popc(m0 & lt)] = ob0;
-            if (k1) wob[n0 + __popc(m1 & lt)] = ob1;
-            __syncwarp();
-            const int cnt = n0 + __popc(m1);
-            *kept_out += (unsigned)cnt;
-            // Four terms at a time: their loads and arithmetic are
-            // independent, only the additions stay in list order.
+        // Four terms at a time: their loads and arithmetic are independent,
+        // only the additions stay in list order.
+        auto score = [&](int cnt) {
             int c = lane;
             for (; c + 3 * LANES < cnt; c += 4 * LANES) {
                 const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
@@ -326,6 +304,84 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
                 bar += e3;
             }
             for (; c < cnt; c += LANES) bar += term(wob[c]);
+        };
+        bool have = false;
+        if (reuse && wl.n >= 0) {
+            const bool in = px >= wl.lx && px <= wl.hx && py >= wl.ly && py <= wl.hy && pz >= wl.lz && pz <= wl.hz;
+            have = __all_sync(0xffffffffu, in);
+        }
+        if (!have) {
+            const unsigned kx = float_key(px), ky = float_key(py), kz = float_key(pz);
+            const float lox = key_float(__reduce_min_sync(0xffffffffu, kx));
+            const float hix = key_float(__reduce_max_sync(0xffffffffu, kx));
+            const float loy = key_float(__reduce_min_sync(0xffffffffu, ky));
+            const float hiy = key_float(__reduce_max_sync(0xffffffffu, ky));
+            const float loz = key_float(__reduce_min_sync(0xffffffffu, kz));
+            const float hiz = key_float(__reduce_max_sync(0xffffffffu, kz));
+            // Test box: the warp's box, enlarged by the margin while a list
+            // is being built.
+            const bool build = wl.n != -2;
+            float tlx = lox, tly = loy, tlz = loz, thx = hix, thy = hiy, thz = hiz;
+            if (build) {
+                tlx -= margin; tly -= margin; tlz -= margin;
+                thx += margin; thy += margin; thz += margin;
+            }
+            auto keep_test = [&](int o, const float4 ob) -> bool {
+                if (o >= M) return false;
+                const float ex = fmaxf(fmaxf(tlx - ob.x, ob.x - thx), 0.0f);
+                const float ey = fmaxf(fmaxf(tly - ob.y, ob.y - thy), 0.0f);
+                const float ez = ob.w >= 0.0f ? fmaxf(fmaxf(tlz - ob.z, ob.z - thz), 0.0f) : 0.0f;
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                return d2 <= (fabsf(ob.w) + C.cull) * 1.0001f;
+            };
+            // Two 32-obstacle chunks are tested at once; kept obstacles are
+            // copied to the warp's list in ascending order.  Building a
+            // list appends all chunks; otherwise each chunk is scored as
+            // soon as it is compacted.
+            const unsigned lt = (1u << wlane) - 1u;
+            int base = 0;
+            bool fits = build;
+            for (int o0 = 0; o0 < M; o0 += 64) {
+                const float4 ob0 = o0 + wlane < M ? so[o0 + wlane] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 ob1 = o0 + 32 + wlane < M ? so[o0 + 32 + wlane] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool k0 = keep_test(o0 + wlane, ob0);
+                const bool k1 = keep_test(o0 + 32 + wlane, ob1);
+                const unsigned m0 = __ballot_sync(0xffffffffu, k0);
+                const unsigned m1 = __ballot_sync(0xffffffffu, k1);
+                const int n0 = __popc(m0);
+                const int cnt = n0 + __popc(m1);
+                if (fits && base + cnt > 64) {
+                    // Too many for one list: score this step chunk by chunk
+                    // with the warp's own box, and stop building lists.
+                    fits = false;
+                    wl.n = -2;
+                    tlx = lox; tly = loy; tlz = loz; thx = hix; thy = hiy; thz = hiz;
+                    o0 = -64;
+                    __syncwarp();
+                    continue;
+                }
+                const int at = fits ? base : 0;
+                if (k0) wob[at + __popc(m0 & lt)] = ob0;
+                if (k1) wob[at + n0 + __popc(m1 & lt)] = ob1;
+                __syncwarp();
+                if (fits) {
+                    base += cnt;
+                } else {
+                    *kept_out += (unsigned)cnt;
+                    score(cnt);
+                    __syncwarp();
+                }
+            }
+            if (fits) {
+                wl.lx = tlx; wl.ly = tly; wl.lz = tlz;
+                wl.hx = thx; wl.hy = thy; wl.hz = thz;
+                wl.n = base;
+                have = true;
+            }
+        }
+        if (have) {
+            *kept_out += (unsigned)wl.n;
+            score(wl.n);
             __syncwarp();
         }
     }
@@ -527,6 +583,10 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
     const DevCost& C = a.C;
     const int n_tiles = a.n_tiles_dev ? *a.n_tiles_dev : a.n_tiles;
     const long long wait_polls = a.wait_polls > 0 ? a.wait_polls : kWaitPolls;
+    // Kept-obstacle lists are reused across steps, except in launches that
+    // count evaluated pairs: those cull every step with the warp's own box.
+    const bool reuse_lists = a.stats == nullptr;
+    const float cull_margin = reuse_lists ? C.cull_margin : 0.0f;
 
     for (int round = 0;; ++round) {
         // ---------------------------------------------------- pick a tile
@@ -634,8 +694,11 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
             int nhit = 0;
             bool hit = false;
             unsigned kept = 0;  // obstacles evaluated by this warp (uniform over the warp)
+            WarpList wl;
+            wl.n = -1;
             kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
-                                 obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, &hit, &kept));
+                                 obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, wl, cull_margin,
+                                                      reuse_lists, &hit, &kept));
             if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
             nhit += hit ? 1 : 0;
             float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -654,7 +717,7 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                 rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
                 step += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
                 step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, wlane, wob,
-                                             &hit, &kept);
+                                             wl, cull_margin, reuse_lists, &hit, &kept);
                 if (C.grid) hit |= grid_hit(C, (x.px - cmp.px) + p0x, (x.py - cmp.py) + p0y, (x.pz - cmp.pz) + p0z);
                 nhit += hit ? 1 : 0;
                 kahan_add(S, Sc, step);
@@ -733,8 +796,11 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                 int nhit = 0;
                 bool hit = false;
                 unsigned kept = 0;
+                WarpList wl;
+                wl.n = -1;
                 kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
-                                     obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, &hit, &kept));
+                                     obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, wl,
+                                                          cull_margin, reuse_lists, &hit, &kept));
                 if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
                 nhit += hit ? 1 : 0;
                 for (int j = 0; j < N; ++j) {
@@ -747,7 +813,8 @@ __global__ void __launch_bounds__(512) mppi_step_kernel(const LaunchArgs a) {
                     mbar_arrive(bar_of(slot, X_EMPTY));
                     const float qpx = a0.x - a1.x, qpy = a0.y - a1.y, qpz = a0.z - a1.z;  // compensated position
                     float step = ok ? a0.w : NAN;
-                    step += obstacle_cost<LANES>(C, qpx, qpy, qpz, sobs, M, lane, wlane, wob, &hit, &kept);
+                    step += obstacle_cost<LANES>(C, qpx, qpy, qpz, sobs, M, lane, wlane, wob, wl, cull_margin,
+                                                 reuse_lists, &hit, &kept);
                     if (C.grid) hit |= grid_hit(C, qpx + p0x, qpy + p0y, qpz + p0z);
                     nhit += hit ? 1 : 0;
                     kahan_add(S, Sc, step);
