@@ -245,6 +245,39 @@ def test_evaluated_pair_counter(M, orc, inp):
         assert_step_close(p, g, orc.mppi_step(p, n_threads=8))
 
 
+@pytest.mark.parametrize("shape", [(128, 1, 0), (256, 1, 1), (128, 2, 0), (384, 2, 1)])
+def test_reused_kept_lists_equal_per_step_culling(M, inp, shape):
+    """A warp's kept-obstacle list is built for its box grown by a margin and
+    reused while its positions stay inside; launches that count evaluated
+    pairs cull every step with the unexpanded box instead.  The obstacles
+    kept only by the margin add exactly +0, so with one lane per sample the
+    per-sample costs and the update are bitwise those of per-step culling
+    (with several lanes the lanes' shares are grouped differently: equal to
+    rounding).  Cases: 64 spheres; 1024 spheres and cylinders (lists that
+    overflow their 64 entries fall back to chunked scoring)."""
+    import torch
+    probs = [inp.eight_with_spheres(K=3000, N=60, M=64, t0=0.7),
+             inp.stress_line(K=2048, N=80)]
+    for prob in probs:
+        outs = []
+        for counting in (False, True):
+            s = M.Solver(prob["model"], prob["params"])
+            s.set_shape(*shape)
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            if counting:
+                s.set_counters(cnt)
+            outs.append(s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"],
+                                want_costs=True))
+            s.close()
+        reuse, per_step = outs
+        if shape[1] == 1:
+            for k in ("costs", "u_out", "u_next", "u_cmd", "x_next"):
+                assert np.array_equal(reuse[k], per_step[k]), (k, prob["params"]["K"])
+        else:
+            c0, c1 = reuse["costs"].astype(np.float64), per_step["costs"].astype(np.float64)
+            assert np.max(np.abs(c0 - c1) / np.maximum(np.abs(c1), 1.0)) <= 1e-6
+
+
 def test_paper_operating_point(M, orc, inp):
     """Table II: K=896, N=15, dt=0.1 s, lambda=1e-4, Sigma=diag(0.60, 0.15,
     0.15, 0.05) as a covariance, Table II weights, motor limits."""
