@@ -229,11 +229,18 @@ int mppi_set_wait_limit(mppi_handle h, int64_t polls, int32_t stall_obstacle_cop
 typedef struct {
     int32_t block;          /* threads per block: 64, 128, 256 or 512       */
     int32_t lanes;          /* lanes per sample: 1 (one thread per sample),
-                               2, 4 or 8 (warp split of the obstacle loop)  */
-    int32_t pipelined;      /* 1 (with lanes == 1): each sample has a
-                               dynamics thread and a cost thread in separate
-                               warps, handing states over through shared-
-                               memory rings (block/2 samples per block)     */
+                               2, 4, 8 or 32 (warp split of the obstacle
+                               loop; 32: one sample per warp)               */
+    int32_t pipelined;      /* 1 (with lanes 1 or 2): each sample has a
+                               dynamics thread and `lanes` cost threads in
+                               separate warps, handing states over through
+                               shared-memory rings (block / (1 + lanes)
+                               samples per block)                           */
+    float list_margin;      /* obstacle tiling: a warp's kept-obstacle list
+                               covers the box of its positions grown by
+                               this many metres and is reused while they
+                               stay inside (0: the default, 1 m; results do
+                               not depend on it beyond FP32 rounding)       */
 } mppi_shape;
 
 /* Forces a launch shape for subsequent calls on the handle (both 0: back

@@ -96,7 +96,7 @@ DevCost make_dev_cost(const mppi_params& p) {
     // ex2.approx.ftz returns exactly 0 below 2^-126: a squared gap beyond
     // 127 / (beta log2 e) contributes nothing (no barrier when beta == 0).
     c.cull = p.beta > 0.0f ? (float)(127.0 / ((double)p.beta * 1.4426950408889634073599)) : INFINITY;
-    c.cull_margin = kCullMargin;
+    c.cull_margin = kCullMargin;  // replaced per launch by the shape's margin
     c.r_uav = p.r_uav;
     c.quat_metric = p.quat_metric; c.tail_mode = p.tail_mode;
     c.shift_alpha = p.shift_alpha; c.delay = p.delay;
@@ -181,7 +181,7 @@ struct mppi_ctx {
 
     Shape forced{0, 0, 0};
     std::map<uint64_t, Shape> table;
-    std::map<uint64_t, GraphEntry> graphs;
+    std::map<std::pair<uint64_t, float>, GraphEntry> graphs;  // (shape and size bucket, list margin)
     cudaStream_t capture_stream = nullptr;
 };
 
@@ -583,10 +583,11 @@ int mppi_set_wait_limit(mppi_handle h, int64_t polls, int32_t stall_obstacle_cop
 int mppi_set_shape(mppi_handle h, const mppi_shape* shape) {
     if (!h || !shape) return MPPI_EINVAL;
     if (shape->block == 0 && shape->lanes == 0) {
-        h->forced = Shape{0, 0, 0};
+        h->forced = Shape{0, 0, 0, 0.0f};
         return MPPI_OK;
     }
-    Shape s{shape->block, shape->lanes, shape->pipelined};
+    if (!(shape->list_margin >= 0.0f && shape->list_margin <= 1e3f)) return MPPI_EINVAL;
+    Shape s{shape->block, shape->lanes, shape->pipelined, shape->list_margin};
     if (!shape_supported(s)) return MPPI_EINVAL;
     h->forced = s;
     return MPPI_OK;
@@ -598,6 +599,7 @@ int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* s
     shape->block = s.block;
     shape->lanes = s.lanes;
     shape->pipelined = s.pipe;
+    shape->list_margin = list_margin(s);
     return MPPI_OK;
 }
 
@@ -708,8 +710,10 @@ int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_
     if ((rc = upload_batch(h, n, plan, st))) return rc;
     const size_t smem = smem_bytes(plan.N_b, plan.M_b, plan.s);
     if (smem > 227 * 1024) return MPPI_EINVAL;
-    const uint64_t key = ((uint64_t)plan.s.block << 48) | ((uint64_t)plan.s.lanes << 40) |
-                         ((uint64_t)plan.s.pipe << 36) | ((uint64_t)plan.N_b << 20) | (uint64_t)plan.M_b;
+    const std::pair<uint64_t, float> key(((uint64_t)plan.s.block << 48) | ((uint64_t)plan.s.lanes << 40) |
+                                             ((uint64_t)plan.s.pipe << 36) | ((uint64_t)plan.N_b << 20) |
+                                             (uint64_t)plan.M_b,
+                                         list_margin(plan.s));
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         GraphEntry g;
@@ -764,32 +768,47 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    // Candidates: one thread or 2/4/8 lanes per sample (blocks 64-512), and
-    // the pipelined form with one or two cost lanes per sample.
+    // Candidates: one thread or 2/4/8/32 lanes per sample (blocks 64-512,
+    // at least 8 samples per block), and the pipelined form with one or two
+    // cost lanes per sample; then, for the fastest of those, the obstacle
+    // tiling (the margin of the warps' kept-obstacle lists).
     std::vector<Shape> cands;
     for (int b : {64, 128, 256, 512})
-        for (int l : {1, 2, 4, 8})
-            if (b / l >= 8) cands.push_back(Shape{b, l, 0});
-    for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 1});
-    for (int b : {192, 384}) cands.push_back(Shape{b, 2, 1});
-    Shape bestS{128, 1, 0};
+        for (int l : {1, 2, 4, 8, 32})
+            if (b / l >= 8) cands.push_back(Shape{b, l, 0, 0.0f});
+    for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 1, 0.0f});
+    for (int b : {192, 384}) cands.push_back(Shape{b, 2, 1, 0.0f});
+    Shape bestS{128, 1, 0, 0.0f};
     float bestT = 1e30f;
     int rc = MPPI_OK;
-    for (const Shape& s : cands) {
-        if (smem_bytes(N, M, s) > 227 * 1024) continue;
-        if ((rc = launch_single(h, in, s, st))) break;  // warm-up
+    auto time_shape = [&](const Shape& s) {
+        if (smem_bytes(N, M, s) > 227 * 1024) return;
+        if ((rc = launch_single(h, in, s, st))) return;  // warm-up
         cudaEventRecord(e0, st);
         for (int r = 0; r < 3; ++r) launch_single(h, in, s, st);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             rc = MPPI_ECUDA;
-            break;
+            return;
         }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < bestT) {
             bestT = ms;
             bestS = s;
+        }
+    };
+    for (const Shape& s : cands) {
+        time_shape(s);
+        if (rc) break;
+    }
+    if (!rc && M > 0) {
+        const Shape base = bestS;
+        for (float m : {0.25f, 0.5f, 2.0f}) {
+            Shape s = base;
+            s.margin = m;
+            time_shape(s);
+            if (rc) break;
         }
     }
     cudaEventDestroy(e0);
@@ -802,6 +821,7 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
         best->block = bestS.block;
         best->lanes = bestS.lanes;
         best->pipelined = bestS.pipe;
+        best->list_margin = list_margin(bestS);
     }
     return MPPI_OK;
 }

@@ -76,10 +76,13 @@ struct DevInstance {
 };
 
 struct Shape {
-    int block;  // threads per block
-    int lanes;  // lanes per sample
-    int pipe;   // 1: pipelined (a dynamics thread and a cost thread per sample)
+    int block;     // threads per block
+    int lanes;     // lanes per sample
+    int pipe;      // 1: pipelined (a dynamics thread and a cost thread per sample)
+    float margin;  // kept-obstacle list margin [m]; 0: kCullMargin
 };
+
+inline float list_margin(const Shape& s) { return s.margin > 0.0f ? s.margin : kCullMargin; }
 
 // Everything one launch of the fused kernel needs.
 struct LaunchArgs {

@@ -1075,7 +1075,7 @@ bool shape_supported(Shape s) {
         const int unit = 32 * (1 + s.lanes);
         return (s.lanes == 1 || s.lanes == 2) && s.block >= unit && s.block <= 512 && s.block % unit == 0;
     }
-    const bool lanes_ok = s.lanes == 1 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8;
+    const bool lanes_ok = s.lanes == 1 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8 || s.lanes == 32;
     const bool block_ok = s.block == 64 || s.block == 128 || s.block == 256 || s.block == 512;
     return s.pipe == 0 && lanes_ok && block_ok;
 }
@@ -1115,7 +1115,9 @@ static cudaError_t launch_t(const LaunchArgs& a, int block, int grid, size_t sme
     return cudaGetLastError();
 }
 
-cudaError_t launch_tiles(const LaunchArgs& a, Shape s, int grid, size_t smem, cudaStream_t st) {
+cudaError_t launch_tiles(const LaunchArgs& args, Shape s, int grid, size_t smem, cudaStream_t st) {
+    LaunchArgs a = args;
+    a.C.cull_margin = list_margin(s);
     if (s.pipe) {
         if (s.lanes == 1) return launch_t<1, true>(a, s.block, grid, smem, st);
         if (s.lanes == 2) return launch_t<2, true>(a, s.block, grid, smem, st);
@@ -1126,6 +1128,7 @@ cudaError_t launch_tiles(const LaunchArgs& a, Shape s, int grid, size_t smem, cu
         case 2: return launch_t<2, false>(a, s.block, grid, smem, st);
         case 4: return launch_t<4, false>(a, s.block, grid, smem, st);
         case 8: return launch_t<8, false>(a, s.block, grid, smem, st);
+        case 32: return launch_t<32, false>(a, s.block, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1147,6 +1150,7 @@ int max_active_blocks(Shape s, size_t smem) {
         case 2: return occupancy_t<2, false>(s.block, smem);
         case 4: return occupancy_t<4, false>(s.block, smem);
         case 8: return occupancy_t<8, false>(s.block, smem);
+        case 32: return occupancy_t<32, false>(s.block, smem);
         default: return 1;
     }
 }

@@ -55,7 +55,7 @@ class Instance(C.Structure):
 
 
 class Shape(C.Structure):
-    _fields_ = [("block", C.c_int32), ("lanes", C.c_int32), ("pipelined", C.c_int32)]
+    _fields_ = [("block", C.c_int32), ("lanes", C.c_int32), ("pipelined", C.c_int32), ("list_margin", C.c_float)]
 
 
 class ServerCfg(C.Structure):
@@ -287,19 +287,24 @@ class Solver:
         _check(fn(self.h, arr, len(instances), _stream_ptr(stream)), "mppi_solve_batch")
 
     # ---------------------------------------------------------- launch shape
-    def set_shape(self, block: int = 0, lanes: int = 0, pipelined: int = 0):
-        s = Shape(block, lanes, pipelined)
+    def set_shape(self, block: int = 0, lanes: int = 0, pipelined: int = 0, list_margin: float = 0.0):
+        """mppi_set_shape: force a launch shape (all 0: back to the tuned or
+        default choice).  list_margin is the obstacle tiling in metres (0:
+        default)."""
+        s = Shape(block, lanes, pipelined, list_margin)
         _check(lib().mppi_set_shape(self.h, C.byref(s)), "mppi_set_shape")
 
     def get_shape(self, K: int, N: int, M: int):
+        """(block, lanes, pipelined, list_margin) used for a problem of size (K, N, M)."""
         s = Shape()
         _check(lib().mppi_get_shape(self.h, K, N, M, C.byref(s)), "mppi_get_shape")
-        return s.block, s.lanes, s.pipelined
+        return s.block, s.lanes, s.pipelined, s.list_margin
 
     def autotune(self, K: int, N: int, M: int, stream=None):
+        """mppi_autotune: the fastest (block, lanes, pipelined, list_margin)."""
         s = Shape()
         _check(lib().mppi_autotune(self.h, K, N, M, C.byref(s), _stream_ptr(stream)), "mppi_autotune")
-        return s.block, s.lanes, s.pipelined
+        return s.block, s.lanes, s.pipelined, s.list_margin
 
 
 def solve_noalloc(model: dict, params: dict, x_hat, ref, obstacles, u_nom, it: int, u_out=None, u_cmd=None,

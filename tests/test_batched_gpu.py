@@ -132,10 +132,11 @@ def test_autotuner_picks_a_supported_shape_and_uses_it(M, orc, inp):
     s = M.Solver(prob["model"], prob["params"])
     before = s.get_shape(3000, 30, 48)
     best = s.autotune(3000, 30, 48)
-    if best[2] == 0:  # one thread or 2/4/8 lanes per sample
-        assert best[0] in (64, 128, 256, 512) and best[1] in (1, 2, 4, 8) and best[0] // best[1] >= 8
+    if best[2] == 0:  # one thread or 2/4/8/32 lanes per sample
+        assert best[0] in (64, 128, 256, 512) and best[1] in (1, 2, 4, 8, 32) and best[0] // best[1] >= 8
     else:  # pipelined: a dynamics warp plus one or two cost warps per 32 samples
         assert best[1] in (1, 2) and best[0] % (32 * (1 + best[1])) == 0 and best[0] <= 512
+    assert best[3] in (0.25, 0.5, 1.0, 2.0)  # obstacle tiling: kept-list margin [m]
     assert s.get_shape(3000, 30, 48) == best
     assert s.get_shape(3000, 30, 0) == s.get_shape(3000, 30, 0)  # other buckets keep their default
     out = s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"], want_costs=True)

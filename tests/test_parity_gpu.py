@@ -129,15 +129,17 @@ def test_nonfinite_state_reports_and_keeps_nominal(M, inp):
 def test_every_launch_shape_matches_and_is_deterministic(M, orc, inp):
     prob = inp.eight_with_spheres(K=3000, N=20, M=40, t0=3.0, **{"lambda": 500.0})
     ref = orc.mppi_step(prob, n_threads=8)
-    shapes = [(b, l, 0) for b in (64, 128, 256, 512) for l in (1, 2, 4, 8)]
-    shapes += [(128, 1, 1), (256, 1, 1), (512, 1, 1), (96, 2, 1), (192, 2, 1), (384, 2, 1)]
-    for block, lanes, pipe in shapes:
-        if True:
-            a = gpu_solve(M, prob, shape=(block, lanes, pipe))
-            assert_step_close(prob, a, ref)
-            b = gpu_solve(M, prob, shape=(block, lanes, pipe))
-            for k in ("u_out", "costs", "u_cmd"):
-                assert np.array_equal(a[k], b[k]), (block, lanes, pipe, k)
+    shapes = [(b, l, 0, 0.0) for b in (64, 128, 256, 512) for l in (1, 2, 4, 8)]
+    shapes += [(64, 32, 0, 0.0), (256, 32, 0, 0.0), (512, 32, 0, 0.0)]
+    shapes += [(128, 1, 1, 0.0), (256, 1, 1, 0.0), (512, 1, 1, 0.0), (96, 2, 1, 0.0), (192, 2, 1, 0.0),
+               (384, 2, 1, 0.0)]
+    shapes += [(128, 1, 0, 0.25), (128, 4, 0, 3.0), (256, 1, 1, 2.0), (256, 32, 0, 0.5)]
+    for shape in shapes:
+        a = gpu_solve(M, prob, shape=shape)
+        assert_step_close(prob, a, ref)
+        b = gpu_solve(M, prob, shape=shape)
+        for k in ("u_out", "costs", "u_cmd"):
+            assert np.array_equal(a[k], b[k]), (shape, k)
 
 
 @pytest.mark.parametrize("K,N,Mo", [(16384, 100, 64), (1000, 1, 3), (257, 7, 0), (3000, 37, 40)])
@@ -245,7 +247,8 @@ def test_evaluated_pair_counter(M, orc, inp):
         assert_step_close(p, g, orc.mppi_step(p, n_threads=8))
 
 
-@pytest.mark.parametrize("shape", [(128, 1, 0), (256, 1, 1), (128, 2, 0), (384, 2, 1)])
+@pytest.mark.parametrize("shape", [(128, 1, 0), (256, 1, 1), (128, 2, 0), (384, 2, 1), (128, 1, 0, 0.25),
+                                   (256, 1, 1, 3.0), (256, 32, 0)])
 def test_reused_kept_lists_equal_per_step_culling(M, inp, shape):
     """A warp's kept-obstacle list is built for its box grown by a margin and
     reused while its positions stay inside; launches that count evaluated
