@@ -388,7 +388,7 @@ def run_serving(args):
     from paper_2407_09812_gb300 import serve
     main = serve.run_fleet(duration_s=args.serve_seconds, n_vehicles=args.serve_vehicles)
     sweep = []
-    for nv in (10, 100):
+    for nv in (1, 10, 100):
         r = serve.run_fleet(duration_s=max(1.0, min(10.0, args.serve_seconds / 3)), n_vehicles=nv, warmup_s=0.5)
         sweep.append({k: r[k] for k in ("workload", "solves_per_s", "rollout_steps_per_s", "latency_ms",
                                         "missed_ticks", "ticks", "mean_batch")})
@@ -413,9 +413,22 @@ def cpu_baseline(seconds: float):
         el = time.perf_counter() - t0
         if el >= seconds or n >= 64:
             break
-    return {"value": K_HEAD * N_HEAD * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+    rate = K_HEAD * N_HEAD * n / el
+    # The same oracle on one core, on a K-subsample of one solve (rollouts
+    # are independent, so rollout-steps/s scale with the sample count).
+    k1 = 1024
+    sub = dict(prob, params=dict(prob["params"], K=k1), ref=refs[0], iter=0)
+    t1 = time.perf_counter()
+    O.mppi_step(sub, n_threads=1)
+    el1 = time.perf_counter() - t1
+    rate1 = k1 * N_HEAD / el1
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} full solves of the headline workload (K=16384, N=100, 64 spheres) in {el:.1f} s",
-            "solves_per_s": n / el}
+            "solves_per_s": n / el,
+            "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                            "sample": f"one solve of the headline workload with K subsampled to {k1} "
+                                      f"in {el1:.2f} s"},
+            "parallel_speedup": rate / rate1}
 
 
 def main():
