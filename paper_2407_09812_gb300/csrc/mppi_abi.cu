@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <new>
 #include <vector>
@@ -166,6 +167,10 @@ struct mppi_ctx {
     float* d_io = nullptr;
     float* h_io = nullptr;
     size_t io_floats = 0;
+    // mppi_solve replayed from a graph [copy in, kernel, copy out], keyed by
+    // everything the captured launch depends on.
+    GraphEntry io_graph;
+    std::array<long long, 6> io_key{};
     cudaStream_t stream = nullptr;
 
     // Occupancy grid applied to every solve of the handle (device pointer
@@ -193,6 +198,9 @@ void drop_graphs(mppi_ctx* h) {
         if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
     }
     h->graphs.clear();
+    if (h->io_graph.exec) cudaGraphExecDestroy(h->io_graph.exec);
+    if (h->io_graph.graph) cudaGraphDestroy(h->io_graph.graph);
+    h->io_graph = GraphEntry{};
 }
 
 bool stream_capturing(cudaStream_t s) {
@@ -633,7 +641,9 @@ int mppi_solve_async(mppi_handle h, const float* x_hat, const float* ref, const 
 }
 
 // Host-buffer solve: inputs packed into one pinned block and one device
-// block, one copy each way.
+// block, one copy each way.  The Philox counter travels in the block too,
+// so [copy in, kernel, copy out] does not change between steps of the same
+// sizes and is replayed from a graph captured on the second such step.
 int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float* obstacles, int32_t M,
                const float* u_nom, uint64_t iter, float* u_out, float* u_cmd, float* u_next, float* x_next,
                float* costs) {
@@ -642,12 +652,14 @@ int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float*
     const int K = h->params.K, N = h->params.N;
     // Layout in floats (16-byte aligned segments).
     auto up4 = [](size_t v) { return (v + 3) / 4 * 4; };
-    const size_t o_x = 0, o_ref = 16, o_obs = up4(o_ref + 13 * (size_t)(N + 1)), o_u = up4(o_obs + 4 * (size_t)M);
+    const size_t o_x = 0, o_it = 14, o_ref = 16, o_obs = up4(o_ref + 13 * (size_t)(N + 1)),
+                 o_u = up4(o_obs + 4 * (size_t)M);
     const size_t in_end = up4(o_u + 4 * (size_t)N);
     const size_t o_uo = in_end, o_uc = up4(o_uo + 4 * (size_t)N), o_un = o_uc + 4, o_xn = up4(o_un + 4 * (size_t)N),
                  o_st = o_xn + 16, o_c = o_st + 4;
     const size_t total = o_c + (costs ? (size_t)K : 0);
     if (total > h->io_floats || !h->h_io) {
+        drop_graphs(h);  // the captured copies name the old blocks
         if (h->h_io) cudaFreeHost(h->h_io);
         if (h->d_io) cudaFree(h->d_io);
         h->h_io = nullptr;
@@ -659,22 +671,64 @@ int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float*
     }
     float* hb = h->h_io;
     std::memcpy(hb + o_x, x_hat, 13 * sizeof(float));
+    std::memcpy(hb + o_it, &iter, sizeof(iter));  // floats 14-15, 8-byte aligned
     std::memcpy(hb + o_ref, ref, 13 * sizeof(float) * (size_t)(N + 1));
     if (M > 0) std::memcpy(hb + o_obs, obstacles, 4 * sizeof(float) * (size_t)M);
     std::memcpy(hb + o_u, u_nom, 4 * sizeof(float) * (size_t)N);
     float* db = h->d_io;
     cudaStream_t st = h->stream;
-    if (cudaMemcpyAsync(db, hb, in_end * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) return MPPI_ECUDA;
-    int32_t* dstatus = reinterpret_cast<int32_t*>(db + o_st);
-    int rc = mppi_solve_async(h, db + o_x, db + o_ref, M > 0 ? db + o_obs : nullptr, M, db + o_u, iter, db + o_uo,
-                              db + o_uc, db + o_un, db + o_xn, costs ? db + o_c : nullptr, dstatus, st);
-    if (rc) {
-        cudaStreamSynchronize(st);
-        return rc;
+    mppi_instance in = instance_from_params(h->params, db + o_x, db + o_ref, M > 0 ? db + o_obs : nullptr, M,
+                                            db + o_u, iter, db + o_uo, db + o_uc, db + o_un, db + o_xn,
+                                            costs ? db + o_c : nullptr, reinterpret_cast<int32_t*>(db + o_st));
+    in.iter_dev = reinterpret_cast<uint64_t*>(db + o_it);
+    int rc = check_instance(in, h);
+    if (rc) return rc;
+    const Shape s = choose_shape(h, in.K, in.N, in.M);
+    const std::array<long long, 6> key{(long long)K, (long long)N, (long long)M, costs ? 1 : 0,
+                                       ((long long)s.block << 32) | ((long long)s.lanes << 8) | s.pipe,
+                                       (long long)(list_margin(s) * 1e6f)};
+    auto enqueue = [&](cudaStream_t q) -> int {
+        if (cudaMemcpyAsync(db, hb, in_end * sizeof(float), cudaMemcpyHostToDevice, q) != cudaSuccess)
+            return MPPI_ECUDA;
+        int r = launch_single(h, in, s, q);
+        if (r) return r;
+        if (cudaMemcpyAsync(hb + in_end, db + in_end, (total - in_end) * sizeof(float), cudaMemcpyDeviceToHost,
+                            q) != cudaSuccess)
+            return MPPI_ECUDA;
+        return MPPI_OK;
+    };
+    if (h->io_graph.exec && h->io_key == key) {
+        if (cudaGraphLaunch(h->io_graph.exec, st) != cudaSuccess) return MPPI_ECUDA;
+    } else {
+        const bool same = h->io_key == key;  // second step of these sizes: capture
+        rc = enqueue(st);
+        if (rc) {
+            cudaStreamSynchronize(st);
+            return rc;
+        }
+        h->io_key = key;
+        if (same && !h->io_graph.exec) {
+            // Capture on the handle's capture stream after this step (buffers
+            // already sized, kernel attributes already set); a failed capture
+            // leaves the plain path in use.
+            if (cudaStreamSynchronize(st) != cudaSuccess) return MPPI_ECUDA;
+            cudaStream_t cs = h->capture_stream;
+            if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const int er = enqueue(cs);
+                cudaGraph_t g = nullptr;
+                const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+                if (!er && ended && g && cudaGraphInstantiate(&h->io_graph.exec, g, 0) == cudaSuccess) {
+                    h->io_graph.graph = g;
+                } else {
+                    if (g) cudaGraphDestroy(g);
+                    h->io_graph = GraphEntry{};
+                    cudaGetLastError();
+                }
+            } else {
+                cudaGetLastError();
+            }
+        }
     }
-    if (cudaMemcpyAsync(hb + in_end, db + in_end, (total - in_end) * sizeof(float), cudaMemcpyDeviceToHost, st) !=
-        cudaSuccess)
-        return MPPI_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return MPPI_ECUDA;
     if (u_out) std::memcpy(u_out, hb + o_uo, 4 * sizeof(float) * (size_t)N);
     if (u_cmd) std::memcpy(u_cmd, hb + o_uc, 4 * sizeof(float));
