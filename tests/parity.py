@@ -7,7 +7,12 @@ Tolerances (FP32 kernel against the FP64 oracle on identical FP32 inputs):
   entries passing through zero are judged on the scale of their noise;
 * samples whose oracle trajectory grazes an obstacle boundary (smallest
   squared gap within 1e-4 m^2) are left out of the cost comparison, because
-  the collision indicator is discontinuous there (their weight is ~0).
+  the collision indicator is discontinuous there (their weight is ~0);
+* the plant state x_next is the plant step of the applied command, which is
+  formed from u_out_0 (R26): it is compared, 1e-4 relative per component
+  (floor 1e-3), with the oracle's plant step of the GPU's own u_out_0, so
+  the comparison measures the step itself and does not re-measure the
+  update's allowed error through it.
 """
 import numpy as np
 
@@ -42,14 +47,24 @@ def state_err(x_gpu, x_orc):
     return float((np.abs(x_gpu - x_orc) / np.maximum(np.abs(x_orc), 1e-3)).max())
 
 
+def plant_step_of(prob, u0):
+    """The oracle's x_next for the applied command formed from u0: clamp,
+    constraint pipeline from x_hat, one RK4 step of shift_alpha * dt."""
+    from oracle import oracle as O
+    m, p = prob["model"], prob["params"]
+    F, tau, _ = O.feasible_input(m, prob["x_hat"], O.clamp_input(m, np.asarray(u0, np.float64)), p["dt"])
+    return O.rk4_step(m, prob["x_hat"], F, tau, p.get("shift_alpha", 1.0) * p["dt"])
+
+
 def compare_step(prob, gpu: dict, orc: dict, check_costs=True):
     """Returns a dict of the worst relative errors of one step."""
     sigma = prob["params"]["sigma"]
+    u_out = np.asarray(gpu["u_out"], np.float64).reshape(-1, 4)
     out = {
         "u_out": control_err(gpu["u_out"], orc["u_out"], sigma),
         "u_next": control_err(gpu["u_next"], orc["u_next"], sigma),
         "u_cmd": control_err(gpu["u_cmd"], orc["u_cmd"], sigma),
-        "x_next": state_err(gpu["x_next"], orc["x_next"]),
+        "x_next": state_err(gpu["x_next"], plant_step_of(prob, u_out[0])),
     }
     if check_costs and gpu.get("costs") is not None:
         out["costs"], out["grazing"] = cost_err(gpu["costs"], orc["costs"], orc.get("min_gap"))

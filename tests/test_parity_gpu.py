@@ -200,6 +200,36 @@ def test_stress_full_size_sampled(M, orc, inp):
     print("stress: sampled cost err", err, "grazing", grazing, "contributors", nz.size)
 
 
+def test_maximum_sizes(M, orc, inp):
+    """The ABI's limits, each at the largest value with the others small:
+    N = N_MAX steps and M = M_MAX obstacles against the full oracle step;
+    K = K_MAX samples with sampled costs and the update checked as
+    sum_k w_k delta_k (weights of the GPU's own costs in FP64, the oracle's
+    noise)."""
+    prob = inp.eight_with_spheres(K=300, N=M.N_MAX, dt=0.002, M=16, t0=0.3, **{"lambda": 100.0})
+    assert_step_close(prob, gpu_solve(M, prob), orc.mppi_step(prob, n_threads=16))
+    prob = inp.eight_with_spheres(K=256, N=8, M=M.M_MAX, t0=0.3, **{"lambda": 100.0})
+    g = gpu_solve(M, prob)
+    assert g["status"] == M.OK
+    assert_step_close(prob, g, orc.mppi_step(prob, n_threads=16))
+    # A low temperature keeps the contributors few enough to sum here.
+    prob = inp.plain_hover(K=M.K_MAX, N=1, seed=3, **{"lambda": 0.005})
+    g = gpu_solve(M, prob)
+    K = prob["params"]["K"]
+    ks = np.unique(np.concatenate([np.arange(0, K, K // 64), [K - 1], np.argsort(g["costs"])[:16]]))
+    c_orc, gap = orc.sample_costs(prob, ks, n_threads=16)
+    err, _ = cost_err(g["costs"][ks], c_orc, gap)
+    assert err <= COST_RTOL, err
+    rc, w = orc.weights(g["costs"].astype(np.float64), prob["params"]["lambda"])
+    nz = np.nonzero(w > 1e-30)[0]
+    assert 0 < nz.size < 200000, nz.size
+    upd = np.zeros((1, 4))
+    for k in nz:
+        upd += w[k] * orc.noise(prob["params"], prob["iter"], int(k), 0)
+    assert control_err(g["u_out"], prob["u_nom"].astype(np.float64) + upd, prob["params"]["sigma"]) <= U_RTOL
+    print("K_MAX: contributors", nz.size)
+
+
 def test_grid_collision_module(M, orc, inp):
     """Occupancy voxel grid as the collision module (with spheres too):
     the GPU's per-state lookup and indicator match the oracle."""
