@@ -253,20 +253,6 @@ __device__ __forceinline__ float ex2_ftz(float x) {
     return y;
 }
 
-// Obstacle term of Sec. IV-D at position p (origin-shifted): returns the
-// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)) and sets *hit_out when
-// the state is inside an obstacle (the indicator is one per state; the
-// caller keeps the count as an exact integer).
-//
-// Exact culling: the warp's positions are bounded by a box (shuffles);
-// each lane tests one obstacle of a 32-obstacle chunk against the box and
-// an obstacle is skipped by the whole warp when, for every position in the
-// box, its squared gap exceeds the cut-off beyond which the FP32 barrier
-// term is exactly zero (and so it cannot be in collision either).  Kept
-// obstacles are processed in ascending order, so the sum equals the
-// uncut sum.  With LANES lanes per sample the lanes of a sample take every
-// LANES-th kept obstacle and combine by xor-shuffles (bitwise identical
-// results on all lanes of the sample).
 // A warp's kept-obstacle list, kept across steps: exact for every position
 // inside the box [l, h] (the warp's box enlarged by a margin when it was
 // built), so it is reused while all of the warp's positions stay inside.
@@ -277,6 +263,24 @@ struct WarpList {
     int n;
 };
 
+// Obstacle term of Sec. IV-D at position p (origin-shifted): returns the
+// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)) and sets *hit_out when
+// the state is inside an obstacle (the indicator is one per state; the
+// caller keeps the count as an exact integer).
+//
+// Exact culling: the warp's positions are bounded by a box (redux.sync
+// min/max on order-preserving keys); each lane tests obstacles of a
+// 32-obstacle chunk against the box, and an obstacle is skipped by the whole
+// warp when, for every position in the box, its squared gap exceeds the
+// cut-off beyond which the FP32 barrier term is exactly zero (and so it
+// cannot be in collision either).  The kept obstacles are copied, in
+// ascending order, into the warp's list (WarpList above), built for the box
+// grown by `margin` and reused while the positions stay inside; obstacles
+// kept only by the margin add exactly +0, so the sum equals the uncut sum.
+// With LANES lanes per sample the lanes of a sample take every LANES-th
+// kept obstacle and combine by xor-shuffles (bitwise identical results on
+// all lanes of the sample).  `reuse` false (launches that count evaluated
+// pairs) culls every step.
 template <int LANES>
 __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float py, float pz, const float4* so,
                                                int M, int lane, int wlane, float4* wob, WarpList& wl,
@@ -502,7 +506,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 constexpr int kRing = 4;
 
 struct SmemLayout {
-    unsigned obs, ref, u, S, e, list, part, wlist, uring, iring, xring, bars, total;
+    unsigned obs, ref, u, S, e, list, part, wlist, xring, bars, total;
 };
 
 __host__ __device__ inline unsigned align_up(unsigned v, unsigned a) { return (v + a - 1) / a * a; }
@@ -520,9 +524,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.e = o;    o = align_up(o + 4u * (unsigned)spb, 128);
     L.list = o; o = align_up(o + 4u * (unsigned)spb, 128);
     L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
-    L.wlist = o; o = align_up(o + 32u * (unsigned)block, 128);
-    L.uring = o;
-    L.iring = o;
+    L.wlist = o; o = align_up(o + 32u * (unsigned)block, 128);  // 64 float4 per warp
     L.xring = o; o = align_up(o + 32u * slots, 128);
     L.bars = o;  o = align_up(o + 8u * 4u * (slots / 32u), 128);
     L.total = o;
