@@ -381,6 +381,70 @@ def run_paper_point(reps=50):
                       "hardware": "Jetson Orin Nano 8 GB (1024-core Ampere GPU at 625 MHz)"}}
 
 
+def run_options(reps=30):
+    """The headline workload with each extension of the paper's method that
+    the kernel implements, one at a time: the exact quaternion angle of
+    Eq. quat_angle, control interpolation (Sec. IV-B, shift_alpha = 0.1),
+    delay compensation (Sec. IV-E, 5 ms), and the occupancy-grid collision
+    module (the 64 spheres rasterised into a 0.1 m voxel grid, 6.5 MB, used
+    alone).  Device buffers, L2 flushed before each solve, median of `reps`
+    solves timed with CUDA events."""
+    import torch
+    from paper_2407_09812_gb300 import mppi
+    dev = torch.device("cuda")
+    prob = headline_problem(0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    x, r, u, o = t(prob["x_hat"]), t(prob["ref"]), t(prob["u_nom"]), t(prob["obstacles"])
+    u_out = torch.zeros(N_HEAD, 4, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # Occupancy grid of the same spheres (inflated by nothing: the grid marks
+    # the obstacles' own volume), 0.1 m voxels over the obstacle box.
+    voxel, origin = 0.1, np.array([-21.0, -11.0, -1.0])
+    shape = (70, 220, 420)  # (z, y, x)
+    centres = [origin[a] + voxel * (np.arange(n) + 0.5) for a, n in ((2, shape[0]), (1, shape[1]), (0, shape[2]))]
+    occ = np.zeros(shape, np.uint8)
+    for c in prob["obstacles"]:
+        lo = [max(0, int((c[a] - c[3] - origin[a]) / voxel)) for a in (2, 1, 0)]
+        hi = [min(n, int((c[a] + c[3] - origin[a]) / voxel) + 2) for a, n in zip((2, 1, 0), shape)]
+        zc, yc, xc = (centres[i][lo[i]:hi[i]] for i in range(3))
+        d2 = ((zc[:, None, None] - c[2]) ** 2 + (yc[None, :, None] - c[1]) ** 2 + (xc[None, None, :] - c[0]) ** 2)
+        occ[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] |= (d2 <= c[3] ** 2).astype(np.uint8)
+    occ_d = t(occ)
+    nz, ny, nx = shape
+    variants = [("as configured", {}, None),
+                ("exact quaternion angle (Eq. quat_angle)", {"quat_metric": 1}, None),
+                ("control interpolation, shift_alpha = 0.1 (Sec. IV-B)", {"shift_alpha": 0.1}, None),
+                ("delay compensation, 5 ms (Sec. IV-E)", {"delay": 0.005}, None),
+                (f"occupancy grid {nx}x{ny}x{nz} at 0.1 m instead of the spheres", {}, "grid")]
+    out = []
+    for name, over, mode in variants:
+        s = mppi.Solver(prob["model"], dict(prob["params"], **over))
+        obs = o
+        if mode == "grid":
+            s.set_grid(occ_d, tuple(origin), voxel)
+            obs = None
+        ts = []
+        for i in range(reps + 3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.solve_async(x, r, obs, u, i, u_out=u_out)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= 3:
+                ts.append(e0.elapsed_time(e1))
+        s.close()
+        ms = float(np.median(ts))
+        entry = {"variant": name, "ms_per_solve": ms, "rollout_steps_per_s": K_HEAD * N_HEAD / (ms * 1e-3)}
+        if mode == "grid":
+            lookups = K_HEAD * (N_HEAD + 1)
+            entry["grid"] = {"bytes": int(occ.size), "lookups_per_solve": lookups,
+                             "lookup_bytes_per_s": lookups / (ms * 1e-3),
+                             "note": "one 1-byte voxel read per state; the grid fits in L2"}
+        out.append(entry)
+    return {"workload": WORKLOAD, "variants": out}
+
+
 def run_serving(args):
     """1000 vehicles at 100 Hz (about 100k requests/s offered, far above one
     GPU's capacity) plus lighter fleets that show the latency below
@@ -441,7 +505,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-vehicles", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sections")
-    ap.add_argument("--section", default="all", choices=["all", "batched", "stress", "serving", "paper"],
+    ap.add_argument("--section", default="all", choices=["all", "batched", "stress", "serving", "paper", "options"],
                     help="run one extra section alone and print its JSON (profiling aid)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -479,7 +543,7 @@ def main():
 
     if args.section != "all":
         fn = {"batched": lambda: run_batched(args), "stress": run_stress, "serving": lambda: run_serving(args),
-              "paper": run_paper_point}
+              "paper": run_paper_point, "options": run_options}
         print(json.dumps({"section": args.section, **fn[args.section]()}), flush=True)
         return
 
@@ -525,6 +589,7 @@ def main():
         line["batched"] = run_batched(args)
         line["stress"] = run_stress()
         line["paper_operating_point"] = run_paper_point()
+        line["options"] = run_options()
         try:
             line["serving"] = run_serving(args)
         except (ImportError, AttributeError, OSError) as e:
