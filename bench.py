@@ -38,12 +38,19 @@ WORKLOAD = ("closed-loop figure-eight tracking, K=16384, N=100, dt=0.01 s, 64 sp
             "per-motor thrust limits, lambda=1")
 
 # Algorithmic FP32 work per rollout-step and per evaluated (state,
-# obstacle) pair, counted from the equations of the method (see the design doc,
-# "Roofline").  Pairs whose barrier term is exactly zero in FP32 and that
-# cannot be in collision are not part of the result and are not counted;
-# the kernel reports how many pairs it evaluated (mppi_set_counters).
+# obstacle) pair, counted from the equations of the method as the oracle
+# writes them: per rollout step noise 24, perturb + clamp 12, input and rate
+# cost 27, constraint pipeline 95, RK4 437, renormalisation 12, tracking
+# cost 43; per pair 17.  Pairs whose barrier term is exactly zero in FP32
+# and that cannot be in collision are not part of the result and are not
+# counted; the kernel reports how many pairs it evaluated (mppi_set_counters).
 FLOP_PER_STEP = 650
 FLOP_PER_PAIR = 17
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the headline kernel in an ncu capture of this workload: the inputs, the
+# partials and the outputs; everything else stays on chip.  Taken for the
+# kernel as it is; set to None when the kernel changes until recaptured.
+HEADLINE_TRAFFIC_BYTES = 114944
 SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -577,7 +584,8 @@ def main():
         "clocks": res["clocks"],
         "status_last_step": res["status"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": HEADLINE_TRAFFIC_BYTES,
+                     "traffic_unit": "bytes per launch (ncu capture)",
                      "kernel": "mppi_step_kernel",
                      "work": {"flop_per_rollout_step": FLOP_PER_STEP, "flop_per_obstacle_pair": FLOP_PER_PAIR,
                               "obstacle_pairs_evaluated_per_solve": res["pairs_per_solve"],
