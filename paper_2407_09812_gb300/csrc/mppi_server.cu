@@ -254,8 +254,11 @@ void dispatcher(mppi_server* s) {
             bool any_busy = false;
             for (Slot& slot : s->slots) any_busy |= slot.busy;
             if (any_busy) {
+                // Batches in flight: poll their events again at once (the
+                // dispatcher owns one host core; a timed sleep would add the
+                // timer's slack, tens of microseconds, to every completion).
                 lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                std::this_thread::yield();
                 lk.lock();
             } else {
                 s->cv.wait_for(lk, std::chrono::milliseconds(2));
