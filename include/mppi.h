@@ -247,10 +247,19 @@ typedef struct {
  * to the tuned/default choice). */
 int mppi_set_shape(mppi_handle h, const mppi_shape* shape);
 
-/* Project autotuner: times every candidate shape on a synthetic problem of
- * size (K, N, M) on `stream`, stores the fastest in the handle's table for
- * that size bucket and returns it in *best (may be NULL).  Synchronous. */
+/* Project autotuner: times every candidate shape (block size, samples per
+ * warp, pipelined form, then the obstacle tiling of the fastest) on a
+ * synthetic problem of size (K, N, M) on `stream`, stores the fastest in
+ * the handle's table for that size bucket and returns it in *best (may be
+ * NULL).  Synchronous. */
 int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* best, void* stream);
+
+/* The same tuning on one of the caller's own problems (DEVICE buffers, as
+ * for mppi_solve_batch; validated the same way).  Its outputs are not
+ * written and its Philox counter is not advanced.  Preferred over the
+ * synthetic problem: the best shape depends on how the obstacles lie
+ * relative to the rollouts, which a synthetic problem does not reproduce. */
+int mppi_autotune_instance(mppi_handle h, const mppi_instance* instance, mppi_shape* best, void* stream);
 
 /* Looks up the shape the handle uses for a problem of size (K, N, M). */
 int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* shape);

@@ -444,6 +444,72 @@ int persistent_grid(Shape s, size_t smem) { return sm_count() * max_active_block
 
 }  // namespace
 
+// Times every candidate shape on one instance (outputs not written) and
+// stores the fastest in the handle's table for the instance's size bucket.
+static int tune_on(mppi_ctx* h, mppi_instance in, cudaStream_t st, mppi_shape* best) {
+    in.u_out = in.u_cmd = in.u_next = in.x_next = in.costs = nullptr;
+    in.status = nullptr;
+    in.iter_dev = nullptr;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // Candidates: one thread or 2/4/8/32 lanes per sample (blocks 64-512,
+    // at least 8 samples per block), and the pipelined form with one or two
+    // cost lanes per sample; then, for the fastest of those, the obstacle
+    // tiling (the margin of the warps' kept-obstacle lists).
+    std::vector<Shape> cands;
+    for (int b : {64, 128, 256, 512})
+        for (int l : {1, 2, 4, 8, 32})
+            if (b / l >= 8) cands.push_back(Shape{b, l, 0, 0.0f});
+    for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 1, 0.0f});
+    for (int b : {192, 384}) cands.push_back(Shape{b, 2, 1, 0.0f});
+    Shape bestS{128, 1, 0, 0.0f};
+    float bestT = 1e30f;
+    int rc = MPPI_OK;
+    auto time_shape = [&](const Shape& s) {
+        if (smem_bytes(in.N, in.M, s) > 227 * 1024) return;
+        if ((rc = launch_single(h, in, s, st))) return;  // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5; ++r) launch_single(h, in, s, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = MPPI_ECUDA;
+            return;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < bestT) {
+            bestT = ms;
+            bestS = s;
+        }
+    };
+    for (const Shape& s : cands) {
+        time_shape(s);
+        if (rc) break;
+    }
+    if (!rc && in.M > 0) {
+        const Shape base = bestS;
+        for (float m : {0.25f, 0.5f, 2.0f}) {
+            Shape s = base;
+            s.margin = m;
+            time_shape(s);
+            if (rc) break;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    if (rc) return rc;
+    h->table[bucket_key(in.K, in.N, in.M)] = bestS;
+    if (best) {
+        best->block = bestS.block;
+        best->lanes = bestS.lanes;
+        best->pipelined = bestS.pipe;
+        best->list_margin = list_margin(bestS);
+    }
+    return MPPI_OK;
+}
+
 extern "C" {
 
 const char* mppi_version(void) { return "gb300-mppi 1.0 (sm_103a)"; }
@@ -806,9 +872,8 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
         obs[4 * o + 2] = 0.5f * (o % 5); obs[4 * o + 3] = (o % 3 == 2) ? -0.5f : 0.6f;
     }
     float* d = nullptr;
-    const size_t o_ref = 16, o_u = o_ref + ref.size() + 4, o_obs = (o_u + u.size() + 3) / 4 * 4 + 4,
-                 o_out = o_obs + obs.size() + 4;
-    const size_t total = o_out + 4 * (size_t)N + 64;
+    const size_t o_ref = 16, o_u = o_ref + ref.size() + 4, o_obs = (o_u + u.size() + 3) / 4 * 4 + 4;
+    const size_t total = o_obs + obs.size() + 4;
     if (cudaMalloc(&d, total * sizeof(float)) != cudaSuccess) return MPPI_ENOMEM;
     cudaMemcpy(d, xh.data(), 13 * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(d + o_ref, ref.data(), ref.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -817,67 +882,18 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
     mppi_params p = h->params;
     p.K = K;
     p.N = N;
-    mppi_instance in = instance_from_params(p, d, d + o_ref, M ? d + o_obs : nullptr, M, d + o_u, 0, d + o_out,
+    mppi_instance in = instance_from_params(p, d, d + o_ref, M ? d + o_obs : nullptr, M, d + o_u, 0, nullptr,
                                             nullptr, nullptr, nullptr, nullptr, nullptr);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    // Candidates: one thread or 2/4/8/32 lanes per sample (blocks 64-512,
-    // at least 8 samples per block), and the pipelined form with one or two
-    // cost lanes per sample; then, for the fastest of those, the obstacle
-    // tiling (the margin of the warps' kept-obstacle lists).
-    std::vector<Shape> cands;
-    for (int b : {64, 128, 256, 512})
-        for (int l : {1, 2, 4, 8, 32})
-            if (b / l >= 8) cands.push_back(Shape{b, l, 0, 0.0f});
-    for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 1, 0.0f});
-    for (int b : {192, 384}) cands.push_back(Shape{b, 2, 1, 0.0f});
-    Shape bestS{128, 1, 0, 0.0f};
-    float bestT = 1e30f;
-    int rc = MPPI_OK;
-    auto time_shape = [&](const Shape& s) {
-        if (smem_bytes(N, M, s) > 227 * 1024) return;
-        if ((rc = launch_single(h, in, s, st))) return;  // warm-up
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < 3; ++r) launch_single(h, in, s, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = MPPI_ECUDA;
-            return;
-        }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < bestT) {
-            bestT = ms;
-            bestS = s;
-        }
-    };
-    for (const Shape& s : cands) {
-        time_shape(s);
-        if (rc) break;
-    }
-    if (!rc && M > 0) {
-        const Shape base = bestS;
-        for (float m : {0.25f, 0.5f, 2.0f}) {
-            Shape s = base;
-            s.margin = m;
-            time_shape(s);
-            if (rc) break;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaStreamSynchronize(st);
+    const int rc = tune_on(h, in, st, best);
     cudaFree(d);
+    return rc;
+}
+
+int mppi_autotune_instance(mppi_handle h, const mppi_instance* instance, mppi_shape* best, void* stream) {
+    if (!h || !instance) return MPPI_EINVAL;
+    int rc = check_instance(*instance, h);
     if (rc) return rc;
-    h->table[bucket_key(K, N, M)] = bestS;
-    if (best) {
-        best->block = bestS.block;
-        best->lanes = bestS.lanes;
-        best->pipelined = bestS.pipe;
-        best->list_margin = list_margin(bestS);
-    }
-    return MPPI_OK;
+    return tune_on(h, *instance, (cudaStream_t)stream, best);
 }
 
 }  // extern "C"

@@ -107,6 +107,7 @@ def lib():
     L.mppi_set_shape.argtypes = [_VP, C.POINTER(Shape)]
     L.mppi_get_shape.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape)]
     L.mppi_autotune.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape), _VP]
+    L.mppi_autotune_instance.argtypes = [_VP, C.POINTER(Instance), C.POINTER(Shape), _VP]
     L.mppi_solve_noalloc.argtypes = [C.POINTER(Model), C.POINTER(Params), _VP, _VP, _VP, C.c_int32, _VP, C.c_uint64,
                                      _VP, _VP, _VP, _VP, _VP, _VP, _VP]
     if hasattr(L, "mppi_server_create"):
@@ -264,11 +265,8 @@ class Solver:
                                     _dptr(costs), _dptr(status), _stream_ptr(stream))
         _check(rc, "mppi_solve_async")
 
-    def solve_batch(self, instances: list, stream=None, graph: bool = False) -> None:
-        """mppi_solve_batch(_graph): instances are dicts of torch CUDA tensors
-        (x_hat, ref, obstacles, u_nom, and any of u_out, u_cmd, u_next,
-        x_next, costs, status, iter_dev) plus K, N, dt, lambda, sigma, seed,
-        stream_id, iter."""
+    @staticmethod
+    def _instances(instances: list):
         arr = (Instance * len(instances))()
         for i, d in enumerate(instances):
             s = arr[i]
@@ -283,6 +281,14 @@ class Solver:
             s.dt, s.lam = float(d["dt"]), float(d["lambda"])
             s.sigma[:] = list(d["sigma"])
             s.seed, s.stream_id, s.reserved = int(d.get("seed", 0)), int(d.get("stream_id", 0)), 0
+        return arr
+
+    def solve_batch(self, instances: list, stream=None, graph: bool = False) -> None:
+        """mppi_solve_batch(_graph): instances are dicts of torch CUDA tensors
+        (x_hat, ref, obstacles, u_nom, and any of u_out, u_cmd, u_next,
+        x_next, costs, status, iter_dev) plus K, N, dt, lambda, sigma, seed,
+        stream_id, iter."""
+        arr = self._instances(instances)
         fn = lib().mppi_solve_batch_graph if graph else lib().mppi_solve_batch
         _check(fn(self.h, arr, len(instances), _stream_ptr(stream)), "mppi_solve_batch")
 
@@ -301,9 +307,18 @@ class Solver:
         return s.block, s.lanes, s.pipelined, s.list_margin
 
     def autotune(self, K: int, N: int, M: int, stream=None):
-        """mppi_autotune: the fastest (block, lanes, pipelined, list_margin)."""
+        """mppi_autotune: the fastest (block, lanes, pipelined, list_margin)
+        on a synthetic problem of size (K, N, M)."""
         s = Shape()
         _check(lib().mppi_autotune(self.h, K, N, M, C.byref(s), _stream_ptr(stream)), "mppi_autotune")
+        return s.block, s.lanes, s.pipelined, s.list_margin
+
+    def autotune_on(self, instance: dict, stream=None):
+        """mppi_autotune_instance: the fastest shape on one of the caller's
+        problems (a dict as for solve_batch; its outputs are not written)."""
+        s = Shape()
+        arr = self._instances([instance])
+        _check(lib().mppi_autotune_instance(self.h, arr, C.byref(s), _stream_ptr(stream)), "mppi_autotune_instance")
         return s.block, s.lanes, s.pipelined, s.list_margin
 
 

@@ -143,3 +143,29 @@ def test_autotuner_picks_a_supported_shape_and_uses_it(M, orc, inp):
     assert_step_close(prob, out, orc.mppi_step(prob, n_threads=8))
     s.close()
     print("autotune", before, "->", best)
+
+
+def test_autotune_on_an_instance_leaves_it_untouched(M, orc, inp):
+    """Tuning on one of the caller's problems: a supported shape is stored
+    for its size bucket, the instance's outputs and device Philox counter
+    are not written, and solving with the tuned shape matches the oracle."""
+    import torch
+    prob = inp.eight_with_spheres(K=4000, N=40, M=64, t0=1.1, **{"lambda": 80.0})
+    d = _device(prob, torch)
+    sentinel = torch.full_like(d["u_out"], 12345.0)
+    d["u_out"].copy_(sentinel)
+    d["u_next"] = d["u_nom"]  # in-place warm start would change the nominal if it ran
+    it = torch.tensor([prob["iter"]], dtype=torch.int64, device="cuda")
+    d["iter_dev"] = it
+    nom = d["u_nom"].clone()
+    s = M.Solver(prob["model"], prob["params"])
+    best = s.autotune_on(d)
+    torch.cuda.synchronize()
+    assert torch.equal(d["u_out"], sentinel) and torch.equal(d["u_nom"], nom)
+    assert int(it.item()) == prob["iter"]
+    assert best[3] in (0.25, 0.5, 1.0, 2.0)
+    assert s.get_shape(4000, 40, 64) == best
+    out = s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"], want_costs=True)
+    assert_step_close(prob, out, orc.mppi_step(prob, n_threads=8))
+    s.close()
+    print("autotune_on", best)
