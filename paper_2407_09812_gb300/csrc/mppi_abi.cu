@@ -860,16 +860,29 @@ int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_
 int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* best, void* stream) {
     if (!h || K < 1 || K > MPPI_K_MAX || N < 1 || N > MPPI_N_MAX || M < 0 || M > MPPI_M_MAX) return MPPI_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    // Synthetic problem: hover reference, start 0.5 m off, M spheres on a
-    // ring 3..8 m away (finite, non-trivial obstacle cost).
+    // Synthetic problem: a level line at 8 m/s through a 40 x 20 x 5 m box of
+    // M obstacles (spheres and, every third, vertical cylinders, radii
+    // 0.3-1.0 m) at fixed pseudo-random places, starting 0.5 m off the line:
+    // the rollouts spread and only nearby obstacles matter, as in flight.
     std::vector<float> xh(13, 0.0f), ref(13 * (size_t)(N + 1), 0.0f), u(4 * (size_t)N, 0.0f), obs(4 * (size_t)M);
-    xh[0] = 0.5f; xh[3] = 1.0f;
-    for (int j = 0; j <= N; ++j) ref[13 * (size_t)j + 3] = 1.0f;
+    const float dt = h->params.dt, speed = 8.0f;
+    xh[0] = -10.0f; xh[1] = 0.5f; xh[2] = 2.5f; xh[3] = 1.0f; xh[7] = speed;
+    for (int j = 0; j <= N; ++j) {
+        float* r = &ref[13 * (size_t)j];
+        r[0] = -10.0f + speed * dt * j; r[2] = 2.5f; r[3] = 1.0f; r[7] = speed;
+    }
     for (int j = 0; j < N; ++j) u[4 * (size_t)j] = h->dm.u_init[0];
+    uint32_t lcg = 12345u;
+    auto unif = [&lcg]() {
+        lcg = lcg * 1664525u + 1013904223u;
+        return (float)(lcg >> 8) * (1.0f / 16777216.0f);
+    };
     for (int o = 0; o < M; ++o) {
-        const float ang = 2.399963f * o, rad = 3.0f + 5.0f * (o % 7) / 7.0f;
-        obs[4 * o + 0] = rad * cosf(ang); obs[4 * o + 1] = rad * sinf(ang);
-        obs[4 * o + 2] = 0.5f * (o % 5); obs[4 * o + 3] = (o % 3 == 2) ? -0.5f : 0.6f;
+        obs[4 * o + 0] = -20.0f + 40.0f * unif();
+        obs[4 * o + 1] = -10.0f + 20.0f * unif();
+        obs[4 * o + 2] = 5.0f * unif();
+        const float rad = 0.3f + 0.7f * unif();
+        obs[4 * o + 3] = (o % 3 == 2) ? -rad : rad;
     }
     float* d = nullptr;
     const size_t o_ref = 16, o_u = o_ref + ref.size() + 4, o_obs = (o_u + u.size() + 3) / 4 * 4 + 4;
