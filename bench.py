@@ -459,7 +459,7 @@ def run_serving(args):
     from paper_2407_09812_gb300 import serve
     main = serve.run_fleet(duration_s=args.serve_seconds, n_vehicles=args.serve_vehicles)
     sweep = []
-    for nv in (1, 10, 100):
+    for nv in (1, 10, 100, 300):
         r = serve.run_fleet(duration_s=max(1.0, min(10.0, args.serve_seconds / 3)), n_vehicles=nv, warmup_s=0.5)
         sweep.append({k: r[k] for k in ("workload", "solves_per_s", "rollout_steps_per_s", "latency_ms",
                                         "missed_ticks", "ticks", "mean_batch")})
