@@ -24,3 +24,15 @@ def orc():
 def inp():
     from paper_2407_09812_gb300 import inputs as I
     return I
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Worst relative errors of the CUDA path against the oracle seen by the
+    parity checks of this session."""
+    try:
+        from parity import WORST
+    except ImportError:
+        return
+    if WORST:
+        terminalreporter.write_line("worst relative errors vs oracle: " +
+                                    ", ".join(f"{k} {v:.2e}" for k, v in sorted(WORST.items())))

@@ -71,8 +71,16 @@ def compare_step(prob, gpu: dict, orc: dict, check_costs=True):
     return out
 
 
+# Worst errors seen by assert_step_close in this session (printed at the end
+# of a GPU run by conftest).
+WORST = {}
+
+
 def assert_step_close(prob, gpu, orc, check_costs=True):
     e = compare_step(prob, gpu, orc, check_costs)
+    for k, v in e.items():
+        if k != "grazing":
+            WORST[k] = max(WORST.get(k, 0.0), float(v))
     assert e["u_out"] <= U_RTOL, e
     assert e["u_next"] <= U_RTOL, e
     assert e["u_cmd"] <= U_RTOL, e
