@@ -767,6 +767,11 @@ int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float*
         if (cudaGraphLaunch(h->io_graph.exec, st) != cudaSuccess) return MPPI_ECUDA;
     } else {
         const bool same = h->io_key == key;  // second step of these sizes: capture
+        if (!same && h->io_graph.exec) {     // captured for other sizes or shape
+            cudaGraphExecDestroy(h->io_graph.exec);
+            cudaGraphDestroy(h->io_graph.graph);
+            h->io_graph = GraphEntry{};
+        }
         rc = enqueue(st);
         if (rc) {
             cudaStreamSynchronize(st);

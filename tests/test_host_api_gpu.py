@@ -1,0 +1,72 @@
+"""The host-buffer solve (mppi_solve) replays [copy in, kernel, copy out]
+from a CUDA graph from the second call of the same sizes on: replayed calls
+give bitwise the results of uncaptured ones, a change of sizes or shape
+recaptures, and the Philox counter passed each call is honoured."""
+import numpy as np
+import pytest
+
+from parity import assert_step_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2407_09812_gb300 import build as B
+    B.build()
+    from paper_2407_09812_gb300 import mppi
+    return mppi
+
+
+def _solve(s, prob, it, obstacles=None):
+    obs = prob["obstacles"] if obstacles is None else obstacles
+    return s.solve(prob["x_hat"], prob["ref"], obs, prob["u_nom"], it, want_costs=True)
+
+
+def test_graph_replay_equals_uncaptured_calls(M, orc, inp):
+    prob = inp.eight_with_spheres(K=3000, N=30, M=24, t0=0.4, **{"lambda": 60.0})
+    s = M.Solver(prob["model"], prob["params"])
+    first = _solve(s, prob, prob["iter"])      # uncaptured
+    _solve(s, prob, prob["iter"] + 1)          # uncaptured, then captured
+    for it in (prob["iter"], prob["iter"] + 7, prob["iter"]):  # replayed
+        out = _solve(s, prob, it)
+        if it == prob["iter"]:
+            for k in ("u_out", "u_cmd", "u_next", "x_next", "costs"):
+                assert np.array_equal(out[k], first[k]), k
+        else:
+            assert_step_close(dict(prob, iter=it), out, orc.mppi_step(dict(prob, iter=it), n_threads=8))
+    s.close()
+
+
+def test_changed_sizes_and_shape_recapture(M, orc, inp):
+    prob = inp.eight_with_spheres(K=2000, N=20, M=16, t0=0.8, **{"lambda": 60.0})
+    s = M.Solver(prob["model"], prob["params"])
+    for _ in range(3):
+        _solve(s, prob, prob["iter"])
+    fewer = prob["obstacles"][:5]
+    p2 = dict(prob, obstacles=fewer)
+    for _ in range(3):  # new obstacle count: plain, capture, replay
+        out = _solve(s, p2, prob["iter"])
+    assert_step_close(p2, out, orc.mppi_step(p2, n_threads=8))
+    s.set_shape(128, 2, 0)
+    for _ in range(3):  # new shape
+        out = _solve(s, prob, prob["iter"])
+    assert_step_close(prob, out, orc.mppi_step(prob, n_threads=8))
+    s.close()
+
+
+def test_shape_validation(M):
+    from paper_2407_09812_gb300 import inputs as I
+    prob = I.plain_hover(K=512, N=10)
+    s = M.Solver(prob["model"], prob["params"])
+    for bad in ((128, 3, 0), (100, 1, 0), (128, 4, 1), (64, 2, 1), (1024, 1, 0), (128, 1, 0, -1.0),
+                (128, 1, 0, float("nan"))):
+        with pytest.raises(M.MppiError):
+            s.set_shape(*bad)
+    s.set_shape(256, 32, 0, 0.5)
+    assert s.get_shape(512, 10, 0) == (256, 32, 0, 0.5)
+    s.set_shape(0, 0, 0)
+    assert s.get_shape(512, 10, 0)[:3] != (256, 32, 0)
+    s.close()
