@@ -169,3 +169,26 @@ def test_autotune_on_an_instance_leaves_it_untouched(M, orc, inp):
     assert_step_close(prob, out, orc.mppi_step(prob, n_threads=8))
     s.close()
     print("autotune_on", best)
+
+
+def test_batch_of_one_and_empty_obstacle_sets(M, orc, inp):
+    """Degenerate batches: one instance (K = 1 and N = 1 included) and
+    instances without obstacles give the alone results and the oracle's."""
+    import torch
+    probs = [inp.plain_hover(K=1, N=1, seed=9), inp.plain_hover(K=33, N=2, seed=8)]
+    for p in probs:
+        s = M.Solver(p["model"], p["params"], _cap([p]))
+        s.set_shape(128, 1, 0)
+        d = _device(p, torch)
+        s.solve_batch([d], graph=True)
+        torch.cuda.synchronize()
+        b = _host(d)
+        assert b["status"] == 0
+        assert_step_close(p, b, orc.mppi_step(p, n_threads=8))
+        a = _device(p, torch)
+        s.solve_async(a["x_hat"], a["ref"], None, a["u_nom"], p["iter"], u_out=a["u_out"], u_cmd=a["u_cmd"],
+                      u_next=a["u_next"], x_next=a["x_next"], costs=a["costs"], status=a["status"])
+        torch.cuda.synchronize()
+        for k in ("u_out", "u_cmd", "u_next", "x_next", "costs"):
+            assert np.array_equal(_host(a)[k], b[k]), k
+        s.close()
