@@ -104,3 +104,29 @@ def test_server_host_validation(built):
     assert not h.value
     assert L.mppi_server_submit(None, 0, None, None, None) == mppi.EINVAL
     assert L.mppi_server_destroy(None) == mppi.EINVAL
+
+
+def test_c_client_compiles_and_struct_layouts_match_the_binding(tmp_path):
+    """The public header compiles as strict C99 in a C program linked against
+    the library, and every public struct has, field by field, the offsets
+    and sizes of the Python binding's ctypes mirrors."""
+    import subprocess
+    from c_client import build_client
+    from paper_2407_09812_gb300 import mppi
+    exe = build_client(str(tmp_path))
+    out = subprocess.run([exe, "layout"], capture_output=True, text=True, check=True).stdout.split("\n")
+    mirrors = {"mppi_model": mppi.Model, "mppi_params": mppi.Params, "mppi_capacity": mppi.Capacity,
+               "mppi_instance": mppi.Instance, "mppi_shape": mppi.Shape, "mppi_server_cfg": mppi.ServerCfg,
+               "mppi_result": mppi.Result, "mppi_server_stats": mppi.ServerStats}
+    seen = set()
+    for line in filter(None, out):
+        struct, field, off, size = line.split()
+        py = mirrors[struct]
+        if field == "-":
+            assert C.sizeof(py) == int(size), (struct, C.sizeof(py), size)
+            continue
+        f = getattr(py, "lam" if field == "lambda" else field)
+        assert (f.offset, f.size) == (int(off), int(size)), (struct, field)
+        seen.add((struct, "lam" if field == "lambda" else field))
+    for struct, py in mirrors.items():
+        assert {(struct, n) for n, _ in py._fields_} <= seen, struct

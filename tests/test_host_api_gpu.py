@@ -70,3 +70,31 @@ def test_shape_validation(M):
     s.set_shape(0, 0, 0)
     assert s.get_shape(512, 10, 0)[:3] != (256, 32, 0)
     s.close()
+
+
+def test_plain_c_client_solves_like_the_binding(M, inp, tmp_path):
+    """A C99 program that includes only include/mppi.h and links the library
+    gets, through mppi_solve, bitwise the results of the Python binding."""
+    import subprocess
+    from c_client import build_client
+    prob = inp.eight_with_spheres(K=2048, N=25, M=12, t0=0.6, **{"lambda": 40.0})
+    exe = build_client(str(tmp_path))
+    N, Mo = prob["params"]["N"], prob["obstacles"].shape[0]
+    blob = (np.int32(Mo).tobytes() + bytes(M.make_model(prob["model"])) + bytes(M.make_params(prob["params"])) +
+            np.ascontiguousarray(prob["x_hat"], np.float32).tobytes() +
+            np.ascontiguousarray(prob["ref"], np.float32).tobytes() +
+            np.ascontiguousarray(prob["obstacles"], np.float32).tobytes() +
+            np.ascontiguousarray(prob["u_nom"], np.float32).tobytes() + np.uint64(prob["iter"]).tobytes())
+    (tmp_path / "in.bin").write_bytes(blob)
+    subprocess.run([exe, "solve", str(tmp_path / "in.bin"), str(tmp_path / "out.bin")], check=True)
+    raw = (tmp_path / "out.bin").read_bytes()
+    status = int(np.frombuffer(raw[:4], np.int32)[0])
+    vals = np.frombuffer(raw[4:], np.float32)
+    u_out, u_cmd = vals[:4 * N].reshape(N, 4), vals[4 * N:4 * N + 4]
+    u_next, x_next = vals[4 * N + 4:8 * N + 4].reshape(N, 4), vals[8 * N + 4:8 * N + 17]
+    s = M.Solver(prob["model"], prob["params"])
+    ref = s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"])
+    s.close()
+    assert status == ref["status"] == 0
+    for a, b in ((u_out, ref["u_out"]), (u_cmd, ref["u_cmd"]), (u_next, ref["u_next"]), (x_next, ref["x_next"])):
+        assert np.array_equal(a, b)
