@@ -99,7 +99,8 @@ def lib():
     L.mppi_set_grid.argtypes = [_VP, _VP, C.c_int32, C.c_int32, C.c_int32, _FP, C.c_float]
     L.mppi_set_counters.argtypes = [_VP, _VP]
     L.mppi_set_wait_limit.argtypes = [_VP, C.c_int64, C.c_int32]
-    L.mppi_solve.argtypes = [_VP, _FP, _FP, _FP, C.c_int32, _FP, C.c_uint64, _FP, _FP, _FP, _FP, _FP]
+    # Pointers passed as addresses (numpy .ctypes.data): the cheapest marshalling.
+    L.mppi_solve.argtypes = [_VP, _VP, _VP, _VP, C.c_int32, _VP, C.c_uint64, _VP, _VP, _VP, _VP, _VP]
     L.mppi_solve_async.argtypes = [_VP, _VP, _VP, _VP, C.c_int32, _VP, C.c_uint64, _VP, _VP, _VP, _VP, _VP, _VP,
                                    _VP]
     L.mppi_solve_batch.argtypes = [_VP, C.POINTER(Instance), C.c_int32, _VP]
@@ -244,12 +245,16 @@ class Solver:
         r = np.ascontiguousarray(ref, np.float32)
         o = np.ascontiguousarray(obstacles, np.float32).reshape(-1, 4)
         u = np.ascontiguousarray(u_nom, np.float32)
-        out = {"u_out": np.zeros((N, 4), np.float32), "u_cmd": np.zeros(4, np.float32),
-               "u_next": np.zeros((N, 4), np.float32), "x_next": np.zeros(13, np.float32),
-               "costs": np.zeros(K, np.float32) if want_costs else None}
-        rc = lib().mppi_solve(self.h, _fptr(x), _fptr(r), _fptr(o) if o.size else None, o.shape[0], _fptr(u), int(it),
-                              _fptr(out["u_out"]), _fptr(out["u_cmd"]), _fptr(out["u_next"]), _fptr(out["x_next"]),
-                              _fptr(out["costs"]))
+        # One allocation for all outputs (each returned array is its own view).
+        n_out = 8 * N + 17 + (K if want_costs else 0)
+        blk = np.empty(n_out, np.float32)
+        base = blk.ctypes.data
+        out = {"u_out": blk[:4 * N].reshape(N, 4), "u_cmd": blk[4 * N:4 * N + 4],
+               "u_next": blk[4 * N + 4:8 * N + 4].reshape(N, 4), "x_next": blk[8 * N + 4:8 * N + 17],
+               "costs": blk[8 * N + 17:] if want_costs else None}
+        rc = lib().mppi_solve(self.h, x.ctypes.data, r.ctypes.data, o.ctypes.data if o.size else None, o.shape[0],
+                              u.ctypes.data, int(it), base, base + 16 * N, base + 16 * N + 16, base + 32 * N + 16,
+                              base + 32 * N + 68 if want_costs else None)
         if rc not in (OK, ENONFINITE):
             raise MppiError(rc, "mppi_solve")
         out["status"] = rc
