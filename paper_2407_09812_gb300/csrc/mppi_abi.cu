@@ -163,6 +163,7 @@ struct mppi_ctx {
     int2* h_tilemap = nullptr;
     int* h_ntiles = nullptr;
     cudaEvent_t ev_staging = nullptr;
+    cudaEvent_t ev_io = nullptr;  // completion of mppi_solve's step
 
     float* d_io = nullptr;
     float* h_io = nullptr;
@@ -558,7 +559,8 @@ int mppi_create(const mppi_model* model, const mppi_params* params, const mppi_c
     h->dc = make_dev_cost(*params);
     if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_staging, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_staging, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_io, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         mppi_destroy(h);
         return MPPI_ECUDA;
@@ -590,6 +592,7 @@ void mppi_destroy(mppi_handle h) {
     if (h->h_ntiles) cudaFreeHost(h->h_ntiles);
     if (h->h_io) cudaFreeHost(h->h_io);
     if (h->ev_staging) cudaEventDestroy(h->ev_staging);
+    if (h->ev_io) cudaEventDestroy(h->ev_io);
     if (h->stream) cudaStreamDestroy(h->stream);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;
@@ -800,7 +803,13 @@ int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float*
             }
         }
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) return MPPI_ECUDA;
+    // Wait for the step by polling its event: the caller is blocked anyway,
+    // and polling sees the completion sooner than a blocking wait.
+    if (cudaEventRecord(h->ev_io, st) != cudaSuccess) return MPPI_ECUDA;
+    cudaError_t q;
+    while ((q = cudaEventQuery(h->ev_io)) == cudaErrorNotReady) {
+    }
+    if (q != cudaSuccess) return MPPI_ECUDA;
     if (u_out) std::memcpy(u_out, hb + o_uo, 4 * sizeof(float) * (size_t)N);
     if (u_cmd) std::memcpy(u_cmd, hb + o_uc, 4 * sizeof(float));
     if (u_next) std::memcpy(u_next, hb + o_un, 4 * sizeof(float) * (size_t)N);
