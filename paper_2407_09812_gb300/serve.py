@@ -58,9 +58,12 @@ class Server:
         mppi._check(mppi.lib().mppi_server_remove_vehicle(self.h, vid), "mppi_server_remove_vehicle")
 
     def submit(self, vid: int, x_hat: np.ndarray, ref: np.ndarray):
-        """Returns the request id, or None when the queue is full."""
+        """Returns the request id, or None when the queue is full.  x_hat
+        (13) and ref ((N+1) x 13) are converted to contiguous float32."""
+        x = np.ascontiguousarray(x_hat, np.float32)
+        r = np.ascontiguousarray(ref, np.float32)
         rid = C.c_uint64()
-        rc = mppi.lib().mppi_server_submit(self.h, vid, _f(x_hat), _f(ref), C.byref(rid))
+        rc = mppi.lib().mppi_server_submit(self.h, vid, _f(x), _f(r), C.byref(rid))
         if rc == mppi.EAGAIN:
             return None
         mppi._check(rc, "mppi_server_submit")
