@@ -169,8 +169,16 @@ def _fptr(a):
     return a.ctypes.data_as(_FP)
 
 
-def _dptr(t):
-    return None if t is None else C.c_void_p(t.data_ptr())
+def _dptr(t, dtype: str = "float32"):
+    """Device address of a torch CUDA tensor, which must be contiguous and of
+    the element type the C ABI expects (float32 data, int32 status, int64
+    counter); None passes NULL."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch." + dtype:
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor, got {t.dtype} on {t.device}"
+                         f"{'' if t.is_contiguous() else ' (not contiguous)'}")
+    return C.c_void_p(t.data_ptr())
 
 
 def _stream_ptr(stream):
@@ -267,7 +275,7 @@ class Solver:
         M = 0 if obstacles is None else obstacles.numel() // 4
         rc = lib().mppi_solve_async(self.h, _dptr(x_hat), _dptr(ref), _dptr(obstacles) if M else None, M,
                                     _dptr(u_nom), int(it), _dptr(u_out), _dptr(u_cmd), _dptr(u_next), _dptr(x_next),
-                                    _dptr(costs), _dptr(status), _stream_ptr(stream))
+                                    _dptr(costs), _dptr(status, "int32"), _stream_ptr(stream))
         _check(rc, "mppi_solve_async")
 
     @staticmethod
@@ -277,10 +285,11 @@ class Solver:
             s = arr[i]
             for f in ("x_hat", "ref", "u_nom", "u_out", "u_cmd", "u_next", "x_next", "costs", "status", "iter_dev"):
                 t = d.get(f)
-                setattr(s, f, t.data_ptr() if t is not None else None)
+                ptr = _dptr(t, "int32" if f == "status" else "int64" if f == "iter_dev" else "float32")
+                setattr(s, f, ptr.value if ptr is not None else None)
             obs = d.get("obstacles")
             M = 0 if obs is None else obs.numel() // 4
-            s.obstacles = obs.data_ptr() if M else None
+            s.obstacles = _dptr(obs).value if M else None
             s.iter = int(d.get("iter", 0))
             s.K, s.N, s.M = int(d["K"]), int(d["N"]), M
             s.dt, s.lam = float(d["dt"]), float(d["lambda"])
@@ -335,7 +344,7 @@ def solve_noalloc(model: dict, params: dict, x_hat, ref, obstacles, u_nom, it: i
     M = 0 if obstacles is None else obstacles.numel() // 4
     rc = lib().mppi_solve_noalloc(C.byref(m), C.byref(p), _dptr(x_hat), _dptr(ref), _dptr(obstacles) if M else None,
                                   M, _dptr(u_nom), int(it), _dptr(u_out), _dptr(u_cmd), _dptr(u_next),
-                                  _dptr(x_next), _dptr(costs), _dptr(status), _stream_ptr(stream))
+                                  _dptr(x_next), _dptr(costs), _dptr(status, "int32"), _stream_ptr(stream))
     _check(rc, "mppi_solve_noalloc")
 
 
