@@ -322,7 +322,11 @@ int mppi_server_add_vehicle(mppi_server* s, int32_t K, int32_t N, float dt, floa
                             const float* obstacles, int32_t M, const float* u_init, uint64_t seed,
                             uint32_t stream_id, int32_t* vehicle_id);
 
-/* Releases a vehicle and its device state once its requests are done. */
+/* Releases a vehicle and its device state once its requests are done:
+ * blocks until the requests already queued or in flight for it complete
+ * (their results stay available to mppi_server_poll).  From the call on,
+ * submissions, exports, imports and removals for the vehicle return
+ * MPPI_ENOTFOUND. */
 int mppi_server_remove_vehicle(mppi_server* s, int32_t vehicle_id);
 
 /* Queues one solve request: state estimate x_hat[13] and reference window

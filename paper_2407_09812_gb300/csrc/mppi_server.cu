@@ -48,6 +48,7 @@ struct Vehicle {
     size_t bytes = 0;
     int in_flight = 0;   // requests dispatched and not completed (0 or 1)
     int queued = 0;      // requests waiting in the queue
+    bool removing = false;  // being removed: its pending requests finish, no new ones
 };
 
 struct Request {
@@ -281,8 +282,10 @@ void destroy_slots(mppi_server* s) {
     s->slots.clear();
 }
 
+// A live vehicle that is not being removed, or NULL.
 Vehicle* find_vehicle(mppi_server* s, int vid) {
-    if (vid < 0 || vid >= (int)s->vehicles.size() || !s->vehicles[vid].live) return nullptr;
+    if (vid < 0 || vid >= (int)s->vehicles.size() || !s->vehicles[vid].live || s->vehicles[vid].removing)
+        return nullptr;
     return &s->vehicles[vid];
 }
 
@@ -405,6 +408,9 @@ int mppi_server_remove_vehicle(mppi_server* s, int32_t vid) {
     std::unique_lock<std::mutex> lk(s->mu);
     Vehicle* v = find_vehicle(s, vid);
     if (!v) return MPPI_ENOTFOUND;
+    // From here on the vehicle takes no new request and a second removal
+    // finds nothing; the requests already queued or in flight complete.
+    v->removing = true;
     s->cv_done.wait(lk, [&] { return v->in_flight == 0 && v->queued == 0; });
     s->bytes_vehicles -= (int64_t)v->bytes;
     s->stats.bytes_in_use = s->bytes_reserved + s->bytes_vehicles;

@@ -156,3 +156,31 @@ def test_admission_budget_and_backpressure(S, inp):
     srv.drain(60000)
     assert srv.stats()["rejected"] >= 1
     srv.close()
+
+
+def test_remove_vehicle_with_pending_requests(S, orc, inp):
+    """Removing a vehicle waits for its queued requests, whose results stay
+    available; the vehicle then takes no more requests, a second removal
+    finds nothing, a vehicle added in its place starts afresh, and the others are
+    unaffected."""
+    from paper_2407_09812_gb300 import mppi
+    probs = _fleet(inp, 3, seed=21)
+    srv = _server(S, inp, 3)
+    vids = [_add(srv, p) for p in probs]
+    rids = [srv.submit(v, p["x_hat"], p["ref"]) for v, p in zip(vids, probs)]
+    srv.remove_vehicle(vids[1])  # returns once its request is done
+    with pytest.raises(mppi.MppiError) as e:
+        srv.submit(vids[1], probs[1]["x_hat"], probs[1]["ref"])
+    assert e.value.code == mppi.ENOTFOUND
+    with pytest.raises(mppi.MppiError):
+        srv.remove_vehicle(vids[1])
+    got = _collect(srv, len(rids))
+    assert set(got) == set(rids) and all(got[r]["status"] == 0 for r in rids)
+    for i in (0, 1, 2):
+        ref = orc.mppi_step(probs[i], n_threads=8)
+        assert control_err(got[rids[i]]["u0"], ref["u_out"][0], probs[i]["params"]["sigma"]) <= U_RTOL
+    v_new = _add(srv, probs[1])
+    r2 = srv.submit(v_new, probs[1]["x_hat"], probs[1]["ref"])
+    got2 = _collect(srv, 1)
+    assert np.array_equal(got2[r2]["u0"], got[rids[1]]["u0"])  # fresh vehicle: same nominal and counter
+    srv.close()
