@@ -474,6 +474,7 @@ int mppi_server_export_vehicle(mppi_server* s, int32_t vid, float* u_nom, uint64
     Vehicle* v = find_vehicle(s, vid);
     if (!v) return MPPI_ENOTFOUND;
     s->cv_done.wait(lk, [&] { return v->in_flight == 0; });
+    if (!v->live || v->removing) return MPPI_ENOTFOUND;  // removed while waiting
     unsigned long long it = 0;
     if (cudaMemcpy(u_nom, v->d_unom, 16 * (size_t)v->N, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(&it, v->d_iter, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -488,6 +489,7 @@ int mppi_server_import_vehicle(mppi_server* s, int32_t vid, const float* u_nom, 
     Vehicle* v = find_vehicle(s, vid);
     if (!v) return MPPI_ENOTFOUND;
     s->cv_done.wait(lk, [&] { return v->in_flight == 0; });
+    if (!v->live || v->removing) return MPPI_ENOTFOUND;  // removed while waiting
     const unsigned long long it = iter;
     if (cudaMemcpy(v->d_unom, u_nom, 16 * (size_t)v->N, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(v->d_iter, &it, 8, cudaMemcpyHostToDevice) != cudaSuccess)
