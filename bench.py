@@ -237,9 +237,13 @@ def run_e2e(args, rank, n_steps):
         if i >= 3:
             lat.append(dt)
     solver.close()
+    # Bytes of the two copies mppi_solve makes (16-byte aligned segments):
+    # in: x_hat and the Philox counter, reference, obstacles, nominal; out:
+    # u_out, u_cmd, u_next, x_next, status.
     N, M = N_HEAD, M_HEAD
-    h2d = 4 * (16 + 13 * (N + 1) + 4 * M + 4 * N + 8)
-    d2h = 4 * (4 * N + 4 + 4 * N + 16 + 4)
+    up4 = lambda v: (v + 3) // 4 * 4
+    h2d = 4 * up4(up4(up4(16 + 13 * (N + 1)) + 4 * M) + 4 * N)
+    d2h = 4 * (up4(4 * N) + 4 + up4(4 * N) + 16 + 4)
     lat = np.array(lat)
     return {"value": K_HEAD * N_HEAD / float(lat.mean()), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": float(lat.mean() * 1e3),
