@@ -26,7 +26,9 @@
  * Ownership: the caller owns every buffer it passes; the library never
  * keeps a caller pointer beyond the call (synchronous entry points) or
  * beyond completion of the work enqueued on the given stream
- * (asynchronous entry points).  A handle owns its device workspace.
+ * (asynchronous entry points), except the occupancy grid of mppi_set_grid
+ * and the counter of mppi_set_counters, which a handle uses until they are
+ * replaced or removed.  A handle owns its device workspace.
  *
  * Errors: every entry point returns MPPI_OK (0) or a negative code.
  * Arguments are validated on the host before any device work is queued;
