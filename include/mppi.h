@@ -141,6 +141,9 @@ int mppi_set_grid(mppi_handle h, const uint8_t* grid, int32_t nx, int32_t ny, in
                   float voxel);
 
 /* One MPPI step with HOST buffers, synchronous (Alg. 1, body of the loop).
+ * The inputs and `iter` are packed into one pinned block, copied in, solved
+ * and copied out on the handle's stream; from the second call with the same
+ * sizes and launch shape on, the three are replayed from a CUDA graph.
  *   x_hat[13]          state estimate x^ (host).
  *   ref[(N+1)*13]      reference x_ref_0..x_ref_N (host).
  *   obstacles[M*4]     obstacle set (host, may be NULL when M == 0).
