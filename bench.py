@@ -369,8 +369,7 @@ def run_paper_point(reps=50):
     from paper_2407_09812_gb300 import inputs as I
     from paper_2407_09812_gb300 import mppi
     dev = torch.device("cuda")
-    sig = tuple(math.sqrt(v) for v in (0.60, 0.15, 0.15, 0.05))
-    prob = I.eight_with_spheres(K=896, N=15, dt=0.1, M=0, **{"lambda": 1e-4, "sigma": sig})
+    prob = I.paper_operating_point()
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     x, r, u = t(prob["x_hat"]), t(prob["ref"]), t(prob["u_nom"])
     uo = torch.zeros(15, 4, device=dev)

@@ -63,6 +63,31 @@ PARAMS_DEFAULT = {
     "stream_id": 0,
 }
 
+# Table I as printed: the simulated vehicle and its control limits (Sim
+# column).  The collective-thrust box is the four rotors' range.
+TABLE_I_VEHICLE = {
+    "mass": 1.21,
+    "arm_l": 0.15,
+    "c_tf": 0.012,
+    "J": (7.06e-3, 7.06e-3, 13.6e-3),
+    "T_min": 0.3,
+    "T_max": 19.0,
+    "F_min": 0.0,
+    "F_max": 4.0 * 19.0,
+    "w_max": (10.0, 10.0, 2.0),
+}
+
+# Table II: the controller settings of the paper's experiments.  Sigma is
+# printed as a diagonal covariance; the noise generator takes standard
+# deviations, so the operating point below passes its square roots.
+TABLE_II_MPPI = {
+    "dt": 0.1,
+    "K": 896,
+    "N": 15,
+    "lambda": 1.0e-4,
+    "Sigma": (0.60, 0.15, 0.15, 0.05),
+}
+
 
 def _f32(v):
     if isinstance(v, (tuple, list)):
@@ -234,6 +259,21 @@ def eight_with_spheres(K=16384, N=100, dt=0.01, M=64, seed=1, t0=0.0, **over) ->
     x = np.zeros(13, np.float32)
     x[:] = ref[0]
     return problem(m, p, x, ref, obs, hover_u(m, N))
+
+
+def paper_operating_point(table1_vehicle=False, M=0, seed=1, offset=(0.0, 0.0, 0.0)) -> dict:
+    """The paper's own operating point (Table II: K=896, N=15, dt=0.1 s,
+    lambda=1e-4, Sigma as a covariance, Table II weights) on the figure
+    eight with per-motor limits; the vehicle is the workload default
+    (1.0 kg, 0..4g) or, with `table1_vehicle`, Table I's simulated one
+    (1.21 kg, rotors 0.3..19 N, yaw rate limit 2 rad/s)."""
+    T = TABLE_II_MPPI
+    over = {"lambda": T["lambda"], "sigma": tuple(math.sqrt(v) for v in T["Sigma"])}
+    if table1_vehicle:
+        over.update(TABLE_I_VEHICLE)
+    prob = eight_with_spheres(K=T["K"], N=T["N"], dt=T["dt"], M=M, seed=seed, **over)
+    prob["x_hat"][0:3] += np.asarray(offset, np.float32)
+    return prob
 
 
 def eight_obstacles_clear_of(traj: "Trajectory", rng, M, t_span, margin=1.2):

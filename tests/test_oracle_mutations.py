@@ -15,7 +15,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mppi_oracle.c")
 PIN_FILES = ["tests/test_oracle_noise.py", "tests/test_oracle_model.py", "tests/test_oracle_cost.py",
-             "tests/test_oracle_softmin.py"]
+             "tests/test_oracle_softmin.py", "tests/test_golden_paper.py"]
 
 # (name, [(original text, mutated text), ...])
 MUTANTS = [

@@ -311,14 +311,13 @@ def test_reused_kept_lists_equal_per_step_culling(M, inp, shape):
             assert np.max(np.abs(c0 - c1) / np.maximum(np.abs(c1), 1.0)) <= 1e-6
 
 
-def test_paper_operating_point(M, orc, inp):
+@pytest.mark.parametrize("table1_vehicle", [False, True])
+def test_paper_operating_point(M, orc, inp, table1_vehicle):
     """Table II: K=896, N=15, dt=0.1 s, lambda=1e-4, Sigma=diag(0.60, 0.15,
-    0.15, 0.05) as a covariance, Table II weights, motor limits."""
-    import math
-    sig = tuple(math.sqrt(v) for v in (0.60, 0.15, 0.15, 0.05))
-    prob = inp.eight_with_spheres(K=896, N=15, dt=0.1, M=0, **{"lambda": 1e-4, "sigma": sig})
-    prob["x_hat"] = prob["x_hat"].copy()
-    prob["x_hat"][0:3] += np.array([0.3, -0.2, 0.1], np.float32)
+    0.15, 0.05) as a covariance, Table II weights, motor limits; on the
+    workload vehicle and on Table I's simulated one (1.21 kg, rotors
+    0.3..19 N, yaw rate limit 2 rad/s)."""
+    prob = inp.paper_operating_point(table1_vehicle=table1_vehicle, offset=(0.3, -0.2, 0.1))
     for it in range(3):
         p = dict(prob, iter=it)
         assert_step_close(p, gpu_solve(M, p), orc.mppi_step(p, n_threads=8))
