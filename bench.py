@@ -485,7 +485,7 @@ def cpu_baseline(seconds: float):
         x, u = r["x_next"].astype(np.float32), r["u_next"].astype(np.float32)
         n += 1
         el = time.perf_counter() - t0
-        if el >= seconds or n >= 64:
+        if el >= seconds or n >= 1024:
             break
     rate = K_HEAD * N_HEAD * n / el
     # The same oracle on one core, on a K-subsample of one solve (rollouts
