@@ -242,9 +242,14 @@ void dispatcher(mppi_server* s) {
             slot.t_launch = now_us();
             lk.unlock();
             const int rc = launch_slot(s, slot);
+            if (rc) {
+                // Copies enqueued before the failure may still read the
+                // slot's staging; the slot is reused only after they end.
+                cudaStreamSynchronize(slot.stream);
+                cudaGetLastError();
+            }
             lk.lock();
             if (rc) {
-                cudaGetLastError();
                 finish_slot(s, slot, rc);
                 s->cv_done.notify_all();
             }

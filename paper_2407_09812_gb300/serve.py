@@ -47,6 +47,8 @@ class Server:
         sig = np.ascontiguousarray(sigma, np.float32)
         obs = np.ascontiguousarray(obstacles, np.float32).reshape(-1, 4)
         ui = None if u_init is None else np.ascontiguousarray(u_init, np.float32)
+        if sig.size != 4 or (ui is not None and ui.size != 4 * int(N)):
+            raise ValueError("sigma needs 4 values and u_init N x 4")
         vid = C.c_int32()
         mppi._check(mppi.lib().mppi_server_add_vehicle(self.h, K, N, dt, lam, _f(sig), _f(obs) if obs.size else None,
                                                        obs.shape[0], _f(ui) if ui is not None else None, seed,
@@ -56,12 +58,16 @@ class Server:
 
     def remove_vehicle(self, vid: int):
         mppi._check(mppi.lib().mppi_server_remove_vehicle(self.h, vid), "mppi_server_remove_vehicle")
+        self.N.pop(vid, None)
 
     def submit(self, vid: int, x_hat: np.ndarray, ref: np.ndarray):
         """Returns the request id, or None when the queue is full.  x_hat
         (13) and ref ((N+1) x 13) are converted to contiguous float32."""
         x = np.ascontiguousarray(x_hat, np.float32)
         r = np.ascontiguousarray(ref, np.float32)
+        N = self.N.get(vid)
+        if x.size != 13 or (N is not None and r.size != 13 * (N + 1)):
+            raise ValueError("x_hat needs 13 values and ref (N+1) x 13 for the vehicle's N")
         rid = C.c_uint64()
         rc = mppi.lib().mppi_server_submit(self.h, vid, _f(x), _f(r), C.byref(rid))
         if rc == mppi.EAGAIN:

@@ -151,6 +151,8 @@ def test_admission_budget_and_backpressure(S, inp):
     srv.close()
     srv = serve_mod.Server(inp.model(), inp.params(), dict(base, hbm_budget_bytes=1 << 30))
     v = _add(srv, probs[0])
+    with pytest.raises(ValueError):  # a reference window of the wrong length never reaches the C side
+        srv.submit(v, probs[0]["x_hat"], probs[0]["ref"][:-1])
     accepted = [srv.submit(v, probs[0]["x_hat"], probs[0]["ref"]) for _ in range(40)]
     assert any(a is None for a in accepted)  # queue full -> MPPI_EAGAIN
     srv.drain(60000)
