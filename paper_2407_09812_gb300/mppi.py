@@ -181,6 +181,35 @@ def _dptr(t, dtype: str = "float32"):
     return C.c_void_p(t.data_ptr())
 
 
+def _sizes(K: int, N: int) -> dict:
+    """Element counts the C ABI reads or writes through each buffer."""
+    return {"x_hat": 13, "ref": 13 * (N + 1), "u_nom": 4 * N, "u_out": 4 * N, "u_cmd": 4, "u_next": 4 * N,
+            "x_next": 13, "costs": K, "status": 1, "iter_dev": 1}
+
+
+def _check_sizes(K: int, N: int, bufs: dict, minimum=("status", "iter_dev")):
+    """Raises ValueError unless every given buffer (numpy array or tensor)
+    holds exactly the elements the call uses (at least, for `minimum`), so
+    that no call reads or writes past a caller's buffer."""
+    want = _sizes(K, N)
+    for name, b in bufs.items():
+        if b is None:
+            continue
+        n = b.size if isinstance(b, np.ndarray) else b.numel()
+        if n != want[name] and not (name in minimum and n >= want[name]):
+            raise ValueError(f"{name}: {n} elements, the step with K={K}, N={N} uses {want[name]}")
+    return bufs
+
+
+def _obstacle_count(obs) -> int:
+    if obs is None:
+        return 0
+    n = obs.size if isinstance(obs, np.ndarray) else obs.numel()
+    if n % 4:
+        raise ValueError(f"obstacles: {n} elements, not a whole number of (cx, cy, cz, r) rows")
+    return n // 4
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch
@@ -251,8 +280,12 @@ class Solver:
         K, N = int(self.params["K"]), int(self.params["N"])
         x = np.ascontiguousarray(x_hat, np.float32)
         r = np.ascontiguousarray(ref, np.float32)
-        o = np.ascontiguousarray(obstacles, np.float32).reshape(-1, 4)
+        o = np.ascontiguousarray(obstacles, np.float32)
         u = np.ascontiguousarray(u_nom, np.float32)
+        if x.size != 13 or r.size != 13 * (N + 1) or u.size != 4 * N or o.size % 4:
+            _obstacle_count(o)
+            _check_sizes(K, N, {"x_hat": x, "ref": r, "u_nom": u})
+        o = o.reshape(-1, 4)
         # One allocation for all outputs (each returned array is its own view).
         n_out = 8 * N + 17 + (K if want_costs else 0)
         blk = np.empty(n_out, np.float32)
@@ -272,7 +305,10 @@ class Solver:
     def solve_async(self, x_hat, ref, obstacles, u_nom, it: int, u_out=None, u_cmd=None, u_next=None, x_next=None,
                     costs=None, status=None, stream=None) -> None:
         """mppi_solve_async: torch CUDA tensors in and out, enqueued on stream."""
-        M = 0 if obstacles is None else obstacles.numel() // 4
+        M = _obstacle_count(obstacles)
+        _check_sizes(int(self.params["K"]), int(self.params["N"]),
+                     dict(x_hat=x_hat, ref=ref, u_nom=u_nom, u_out=u_out, u_cmd=u_cmd, u_next=u_next,
+                          x_next=x_next, costs=costs, status=status))
         rc = lib().mppi_solve_async(self.h, _dptr(x_hat), _dptr(ref), _dptr(obstacles) if M else None, M,
                                     _dptr(u_nom), int(it), _dptr(u_out), _dptr(u_cmd), _dptr(u_next), _dptr(x_next),
                                     _dptr(costs), _dptr(status, "int32"), _stream_ptr(stream))
@@ -283,12 +319,13 @@ class Solver:
         arr = (Instance * len(instances))()
         for i, d in enumerate(instances):
             s = arr[i]
+            _check_sizes(int(d["K"]), int(d["N"]), {f: d.get(f) for f in _sizes(1, 1)})
             for f in ("x_hat", "ref", "u_nom", "u_out", "u_cmd", "u_next", "x_next", "costs", "status", "iter_dev"):
                 t = d.get(f)
                 ptr = _dptr(t, "int32" if f == "status" else "int64" if f == "iter_dev" else "float32")
                 setattr(s, f, ptr.value if ptr is not None else None)
             obs = d.get("obstacles")
-            M = 0 if obs is None else obs.numel() // 4
+            M = _obstacle_count(obs)
             s.obstacles = _dptr(obs).value if M else None
             s.iter = int(d.get("iter", 0))
             s.K, s.N, s.M = int(d["K"]), int(d["N"]), M
@@ -341,7 +378,10 @@ def solve_noalloc(model: dict, params: dict, x_hat, ref, obstacles, u_nom, it: i
     """mppi_solve_noalloc: the allocation-free step (no handle; scratch in a
     fixed device array; K <= 32768, N <= 256).  torch CUDA tensors in/out."""
     m, p = make_model(model), make_params(params)
-    M = 0 if obstacles is None else obstacles.numel() // 4
+    M = _obstacle_count(obstacles)
+    _check_sizes(int(params["K"]), int(params["N"]),
+                 dict(x_hat=x_hat, ref=ref, u_nom=u_nom, u_out=u_out, u_cmd=u_cmd, u_next=u_next, x_next=x_next,
+                      costs=costs, status=status))
     rc = lib().mppi_solve_noalloc(C.byref(m), C.byref(p), _dptr(x_hat), _dptr(ref), _dptr(obstacles) if M else None,
                                   M, _dptr(u_nom), int(it), _dptr(u_out), _dptr(u_cmd), _dptr(u_next),
                                   _dptr(x_next), _dptr(costs), _dptr(status, "int32"), _stream_ptr(stream))

@@ -130,3 +130,26 @@ def test_c_client_compiles_and_struct_layouts_match_the_binding(tmp_path):
         seen.add((struct, "lam" if field == "lambda" else field))
     for struct, py in mirrors.items():
         assert {(struct, n) for n, _ in py._fields_} <= seen, struct
+
+
+def test_binding_refuses_buffers_that_do_not_match_the_step(built):
+    """The C ABI takes plain pointers and cannot see a buffer's length, so
+    the Python binding checks every buffer against K and N before a call:
+    a short reference window or a ragged obstacle array never reaches the
+    library."""
+    import numpy as np
+    from paper_2407_09812_gb300 import mppi
+    K, N = 64, 7
+    good = {"x_hat": np.zeros(13), "ref": np.zeros((N + 1, 13)), "u_nom": np.zeros((N, 4)),
+            "u_out": np.zeros((N, 4)), "u_cmd": np.zeros(4), "u_next": np.zeros((N, 4)), "x_next": np.zeros(13),
+            "costs": np.zeros(K), "status": np.zeros(1), "iter_dev": np.zeros(1)}
+    assert mppi._check_sizes(K, N, good) is good
+    for name in good:
+        for n in (good[name].size - 1, good[name].size + 1):
+            if n < 1 or (name in ("status", "iter_dev") and n > good[name].size):
+                continue  # status and the counter may be longer than one element
+            with pytest.raises(ValueError, match=name):
+                mppi._check_sizes(K, N, dict(good, **{name: np.zeros(n)}))
+    assert mppi._obstacle_count(None) == 0 and mppi._obstacle_count(np.zeros((5, 4))) == 5
+    with pytest.raises(ValueError):
+        mppi._obstacle_count(np.zeros(9))

@@ -64,11 +64,17 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     import torch
     from paper_2407_09812_gb300 import inputs as I
     from paper_2407_09812_gb300 import mppi
-    big = I.plain_hover(K=40000, N=10)
     x = torch.zeros(13, device="cuda")
+    big = I.plain_hover(K=40000, N=10)
     with pytest.raises(mppi.MppiError) as e:
-        mppi.solve_noalloc(big["model"], big["params"], x, x, None, x, 0)
+        mppi.solve_noalloc(big["model"], big["params"], x, torch.zeros(11, 13, device="cuda"), None,
+                           torch.zeros(10, 4, device="cuda"), 0)
     assert e.value.code == mppi.EINVAL
     long = I.plain_hover(K=100, N=300)
     with pytest.raises(mppi.MppiError):
-        mppi.solve_noalloc(long["model"], long["params"], x, x, None, x, 0)
+        mppi.solve_noalloc(long["model"], long["params"], x, torch.zeros(301, 13, device="cuda"), None,
+                           torch.zeros(300, 4, device="cuda"), 0)
+    # Buffers that do not match K and N are refused before any call.
+    ok = I.plain_hover(K=100, N=10)
+    with pytest.raises(ValueError):
+        mppi.solve_noalloc(ok["model"], ok["params"], x, x, None, x, 0)
