@@ -85,7 +85,8 @@ typedef struct {
     float Rd[4];       /* input-change weight diagonal (Eq. cost)           */
     float c_obs;       /* collision indicator weight (Sec. IV-D)            */
     float c_bar;       /* exponential barrier weight                        */
-    float beta;        /* barrier rate [1/m^2]: c_bar exp(-beta max(gap,0)) */
+    float beta;        /* barrier rate [1/m^2]: c_bar exp(-beta max(gap,0)),
+                          a term below 2^-48 c_bar counts as 0               */
     float r_uav;       /* vehicle radius added to every obstacle [m]        */
     int32_t quat_metric; /* 0: 1-<q,q_ref>^2 (Eq. quat_approx);
                             1: acos(2<q,q_ref>^2-1) (Eq. quat_angle)        */
@@ -214,8 +215,8 @@ int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_
 /* Measurement hook (the paper has no counterpart): with a DEVICE counter
  * set, every later launch of the handle adds to counters[0] the number of
  * (rollout state, obstacle) pairs it evaluated after its exact culling
- * (pairs whose barrier term is exactly zero in FP32 and that cannot be in
- * collision are skipped).  Used to state the roofline in work actually
+ * (pairs whose barrier term is below its floor, 2^-48 of c_bar, where it
+ * counts as zero, and that cannot be in collision are skipped).  Used to state the roofline in work actually
  * required.  NULL turns it off.  The counter must be 8-byte aligned. */
 int mppi_set_counters(mppi_handle h, uint64_t* counters);
 

@@ -94,9 +94,10 @@ DevCost make_dev_cost(const mppi_params& p) {
     for (int i = 0; i < 4; ++i) { c.R[i] = p.R[i]; c.Rd[i] = p.Rd[i]; }
     c.c_obs = p.c_obs; c.c_bar = p.c_bar;
     c.beta_log2e = (float)((double)p.beta * 1.4426950408889634073599);
-    // ex2.approx.ftz returns exactly 0 below 2^-126: a squared gap beyond
-    // 127 / (beta log2 e) contributes nothing (no barrier when beta == 0).
-    c.cull = p.beta > 0.0f ? (float)(127.0 / ((double)p.beta * 1.4426950408889634073599)) : INFINITY;
+    // A squared gap beyond kBarrierFloorLog2 / (beta log2 e) puts the term
+    // below its floor, where it counts as 0 (no barrier when beta == 0).
+    c.cull = p.beta > 0.0f ? (float)((double)kBarrierFloorLog2 / ((double)p.beta * 1.4426950408889634073599))
+                           : INFINITY;
     c.cull_margin = kCullMargin;  // replaced per launch by the shape's margin
     c.r_uav = p.r_uav;
     c.quat_metric = p.quat_metric; c.tail_mode = p.tail_mode;

@@ -38,11 +38,19 @@ struct DevModel {
 // inside; a larger margin means fewer rebuilds but more (exactly zero) terms.
 constexpr float kCullMargin = 1.0f;  // [m]
 
+// Floor of the obstacle barrier: a term exp(-beta max(s, 0)) below
+// 2^-kBarrierFloorLog2 counts as exactly zero.  Per obstacle and state that
+// drops at most 2^-48 c_bar (3.6e-13 at c_bar = 100), far below the FP32
+// resolution of any rollout cost; in exchange an obstacle whose squared gap
+// exceeds kBarrierFloorLog2 / (beta log2 e) (5.9 m + r at beta = 1) is
+// skipped, against 9.4 m + r where the FP32 exponential itself reaches 0.
+constexpr float kBarrierFloorLog2 = 48.0f;
+
 struct DevCost {
     float c_p, c_q, c_v, c_w;
     float R[4], Rd[4];
     float c_obs, c_bar, beta_log2e, r_uav;
-    float cull;             // squared-gap beyond which the barrier is exactly 0 (FP32)
+    float cull;             // squared gap beyond which the barrier term is below its floor (counts as 0)
     float cull_margin;      // enlargement of a warp's box when its kept-obstacle list is built [m]
     int quat_metric, tail_mode;
     float shift_alpha, delay;

@@ -264,19 +264,20 @@ struct WarpList {
 };
 
 // Obstacle term of Sec. IV-D at position p (origin-shifted): returns the
-// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)) and sets *hit_out when
-// the state is inside an obstacle (the indicator is one per state; the
-// caller keeps the count as an exact integer).
+// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)), each term below its
+// floor 2^-kBarrierFloorLog2 taken as 0, and sets *hit_out when the state is
+// inside an obstacle (the indicator is one per state; the caller keeps the
+// count as an exact integer).
 //
 // Exact culling: the warp's positions are bounded by a box (redux.sync
 // min/max on order-preserving keys); each lane tests obstacles of a
 // 32-obstacle chunk against the box, and an obstacle is skipped by the whole
 // warp when, for every position in the box, its squared gap exceeds the
-// cut-off beyond which the FP32 barrier term is exactly zero (and so it
-// cannot be in collision either).  The kept obstacles are copied, in
-// ascending order, into the warp's list (WarpList above), built for the box
-// grown by `margin` and reused while the positions stay inside; obstacles
-// kept only by the margin add exactly +0, so the sum equals the uncut sum.
+// cut-off beyond which the term is below its floor (and so it cannot be in
+// collision either).  The kept obstacles are copied, in ascending order,
+// into the warp's list (WarpList above), built for the box grown by
+// `margin` and reused while the positions stay inside; obstacles kept only
+// by the margin add exactly +0, so the sum equals the uncut sum.
 // With LANES lanes per sample the lanes of a sample take every LANES-th
 // kept obstacle and combine by xor-shuffles (bitwise identical results on
 // all lanes of the sample).  `reuse` false (launches that count evaluated
@@ -288,12 +289,18 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
     float bar = 0.0f;
     bool hit = false;
     if (M > 0) {
+        // term: the exponent -beta log2(e) max(gap, 0) of one obstacle;
+        // add: its barrier term, exactly 0 below the floor whichever box
+        // kept the obstacle, so the sum does not depend on the culling.
         auto term = [&](const float4 ob) {
             const float dx = px - ob.x, dy = py - ob.y, dz = pz - ob.z;
             const float sph = ob.w >= 0.0f ? dz : 0.0f;  // vertical cylinders ignore z
             const float sg = fmaf(dx, dx, fmaf(dy, dy, sph * dz)) - fabsf(ob.w);
             hit |= (sg <= 0.0f);
-            return ex2_ftz(-C.beta_log2e * fmaxf(sg, 0.0f));
+            return -C.beta_log2e * fmaxf(sg, 0.0f);
+        };
+        auto add = [&](const float a) {
+            if (a >= -kBarrierFloorLog2) bar += ex2_ftz(a);
         };
         // Four terms at a time: their loads and arithmetic are independent,
         // only the additions stay in list order.
@@ -301,13 +308,13 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
             int c = lane;
             for (; c + 3 * LANES < cnt; c += 4 * LANES) {
                 const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
-                const float e0 = term(q0), e1 = term(q1), e2 = term(q2), e3 = term(q3);
-                bar += e0;
-                bar += e1;
-                bar += e2;
-                bar += e3;
+                const float a0 = term(q0), a1 = term(q1), a2 = term(q2), a3 = term(q3);
+                add(a0);
+                add(a1);
+                add(a2);
+                add(a3);
             }
-            for (; c < cnt; c += LANES) bar += term(wob[c]);
+            for (; c < cnt; c += LANES) add(term(wob[c]));
         };
         bool have = false;
         if (reuse && wl.n >= 0) {
