@@ -1084,7 +1084,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
 // One thread per sample in blocks of at most 128 threads (the batched
 // launches' default) runs the instantiation that fits 6 blocks per SM: 24
 // warps instead of 16 raise the issue rate of these issue-bound launches
-// (256 uneven instances: 7.52 -> 7.23 ms; 80 registers, 8 bytes spilled).
+// (256 uneven instances: 7.52 -> 7.23 ms; at most 85 registers, no spills).
 constexpr int kMinBlocks128 = 6;
 
 bool shape_supported(Shape s) {
