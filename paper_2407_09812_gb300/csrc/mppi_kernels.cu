@@ -258,10 +258,16 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 // built), so it is reused while all of the warp's positions stay inside.
 // Replicated in every lane.  n = -1: no list yet; -2: a list did not fit
 // (more than 64 kept), lists are not used for the rest of the rollout.
+// np >= n: the list's length after padding (see obstacle_cost).
 struct WarpList {
     float lx, ly, lz, hx, hy, hz;
-    int n;
+    int n, np;
 };
+
+// Padding entry of a kept-obstacle list: its squared gap overflows to
+// +inf, so its term is below the floor (never added) and it is never in
+// collision.
+constexpr float kFarObstacle = 1.0e30f;
 
 // Obstacle term of Sec. IV-D at position p (origin-shifted): returns the
 // barrier sum c_bar sum_o exp(-beta max(gap_o, 0)), each term below its
@@ -302,10 +308,25 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
         auto add = [&](const float a) {
             if (a >= -kBarrierFloorLog2) bar += ex2_ftz(a);
         };
-        // Four terms at a time: their loads and arithmetic are independent,
-        // only the additions stay in list order.
+        // Eight (then four) terms at a time: their loads and arithmetic are
+        // independent, only the additions stay in list order.
         auto score = [&](int cnt) {
             int c = lane;
+            for (; c + 7 * LANES < cnt; c += 8 * LANES) {
+                const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
+                const float4 q4 = wob[c + 4 * LANES], q5 = wob[c + 5 * LANES], q6 = wob[c + 6 * LANES],
+                             q7 = wob[c + 7 * LANES];
+                const float a0 = term(q0), a1 = term(q1), a2 = term(q2), a3 = term(q3);
+                const float a4 = term(q4), a5 = term(q5), a6 = term(q6), a7 = term(q7);
+                add(a0);
+                add(a1);
+                add(a2);
+                add(a3);
+                add(a4);
+                add(a5);
+                add(a6);
+                add(a7);
+            }
             for (; c + 3 * LANES < cnt; c += 4 * LANES) {
                 const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
                 const float a0 = term(q0), a1 = term(q1), a2 = term(q2), a3 = term(q3);
@@ -315,6 +336,16 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
                 add(a3);
             }
             for (; c < cnt; c += LANES) add(term(wob[c]));
+        };
+        // Fills list entries [cnt, padded) with far-away padding so that
+        // the scoring loop runs only whole groups of four independent terms
+        // (a leftover term runs alone, with the full latency of its chain).
+        auto pad = [&](int cnt) -> int {
+            const int padded = min((cnt + 4 * LANES - 1) / (4 * LANES) * (4 * LANES), 64);
+            for (int i = cnt + wlane; i < padded; i += 32)
+                wob[i] = make_float4(kFarObstacle, kFarObstacle, kFarObstacle, 0.0f);
+            __syncwarp();
+            return padded;
         };
         bool have = false;
         if (reuse && wl.n >= 0) {
@@ -379,7 +410,7 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
                     base += cnt;
                 } else {
                     *kept_out += (unsigned)cnt;
-                    score(cnt);
+                    score(pad(cnt));
                     __syncwarp();
                 }
             }
@@ -387,12 +418,13 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
                 wl.lx = tlx; wl.ly = tly; wl.lz = tlz;
                 wl.hx = thx; wl.hy = thy; wl.hz = thz;
                 wl.n = base;
+                wl.np = pad(base);
                 have = true;
             }
         }
         if (have) {
             *kept_out += (unsigned)wl.n;
-            score(wl.n);
+            score(wl.np);
             __syncwarp();
         }
     }
@@ -708,6 +740,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             unsigned kept = 0;  // obstacles evaluated by this warp (uniform over the warp)
             WarpList wl;
             wl.n = -1;
+            wl.np = 0;
             kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
                                  obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, wl, cull_margin,
                                                       reuse_lists, &hit, &kept));
@@ -810,6 +843,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 unsigned kept = 0;
                 WarpList wl;
                 wl.n = -1;
+                wl.np = 0;
                 kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
                                      obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, wl,
                                                           cull_margin, reuse_lists, &hit, &kept));
