@@ -269,11 +269,14 @@ struct WarpList {
 // collision.
 constexpr float kFarObstacle = 1.0e30f;
 
-// Obstacle term of Sec. IV-D at position p (origin-shifted): returns the
-// barrier sum c_bar sum_o exp(-beta max(gap_o, 0)), each term below its
-// floor 2^-kBarrierFloorLog2 taken as 0, and sets *hit_out when the state is
-// inside an obstacle (the indicator is one per state; the caller keeps the
-// count as an exact integer).
+// Obstacle term of Sec. IV-D at NP positions p[i] (origin-shifted) of the
+// lane's sample: bar_out[i] = the barrier sum c_bar sum_o exp(-beta
+// max(gap_o, 0)), each term below its floor 2^-kBarrierFloorLog2 taken as 0,
+// and hit_out[i] = whether p[i] is inside an obstacle (the indicator is one
+// per state; the caller keeps the count as an exact integer).  NP = 2 scores
+// two states of a rollout against one pass over the list: the same terms in
+// the same order as two single calls, with twice the independent work per
+// loaded obstacle.
 //
 // Exact culling: the warp's positions are bounded by a box (redux.sync
 // min/max on order-preserving keys); each lane tests obstacles of a
@@ -288,54 +291,78 @@ constexpr float kFarObstacle = 1.0e30f;
 // kept obstacle and combine by xor-shuffles (bitwise identical results on
 // all lanes of the sample).  `reuse` false (launches that count evaluated
 // pairs) culls every step.
-template <int LANES>
-__device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float py, float pz, const float4* so,
-                                               int M, int lane, int wlane, float4* wob, WarpList& wl,
-                                               float margin, bool reuse, bool* hit_out, unsigned* kept_out) {
-    float bar = 0.0f;
-    bool hit = false;
+template <int LANES, int NP>
+__device__ __forceinline__ void obstacle_cost_n(const DevCost& C, const float (&px)[NP], const float (&py)[NP],
+                                                const float (&pz)[NP], const float4* so, int M, int lane, int wlane,
+                                                float4* wob, WarpList& wl, float margin, bool reuse,
+                                                float (&bar_out)[NP], bool (&hit_out)[NP], unsigned* kept_out) {
+    float bar[NP];
+    bool hit[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        bar[i] = 0.0f;
+        hit[i] = false;
+    }
     if (M > 0) {
-        // term: the exponent -beta log2(e) max(gap, 0) of one obstacle;
-        // add: its barrier term, exactly 0 below the floor whichever box
-        // kept the obstacle, so the sum does not depend on the culling.
-        auto term = [&](const float4 ob) {
-            const float dx = px - ob.x, dy = py - ob.y, dz = pz - ob.z;
+        // term: the exponent -beta log2(e) max(gap, 0) of one obstacle at
+        // position i; add: its barrier term, exactly 0 below the floor
+        // whichever box kept the obstacle, so the sum does not depend on the
+        // culling.
+        auto term = [&](const float4 ob, const int i) {
+            const float dx = px[i] - ob.x, dy = py[i] - ob.y, dz = pz[i] - ob.z;
             const float sph = ob.w >= 0.0f ? dz : 0.0f;  // vertical cylinders ignore z
             const float sg = fmaf(dx, dx, fmaf(dy, dy, sph * dz)) - fabsf(ob.w);
-            hit |= (sg <= 0.0f);
+            hit[i] |= (sg <= 0.0f);
             return -C.beta_log2e * fmaxf(sg, 0.0f);
         };
-        auto add = [&](const float a) {
-            if (a >= -kBarrierFloorLog2) bar += ex2_ftz(a);
+        auto add = [&](const float a, const int i) {
+            if (a >= -kBarrierFloorLog2) bar[i] += ex2_ftz(a);
         };
-        // Eight (then four) terms at a time: their loads and arithmetic are
-        // independent, only the additions stay in list order.
+        // Eight terms at a time (one position: eight obstacles, then four;
+        // two positions: four obstacles each): their loads and arithmetic
+        // are independent, only the additions stay in list order.
         auto score = [&](int cnt) {
             int c = lane;
-            for (; c + 7 * LANES < cnt; c += 8 * LANES) {
-                const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
-                const float4 q4 = wob[c + 4 * LANES], q5 = wob[c + 5 * LANES], q6 = wob[c + 6 * LANES],
-                             q7 = wob[c + 7 * LANES];
-                const float a0 = term(q0), a1 = term(q1), a2 = term(q2), a3 = term(q3);
-                const float a4 = term(q4), a5 = term(q5), a6 = term(q6), a7 = term(q7);
-                add(a0);
-                add(a1);
-                add(a2);
-                add(a3);
-                add(a4);
-                add(a5);
-                add(a6);
-                add(a7);
+            if (NP == 1) {
+                for (; c + 7 * LANES < cnt; c += 8 * LANES) {
+                    const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
+                    const float4 q4 = wob[c + 4 * LANES], q5 = wob[c + 5 * LANES], q6 = wob[c + 6 * LANES],
+                                 q7 = wob[c + 7 * LANES];
+                    const float a0 = term(q0, 0), a1 = term(q1, 0), a2 = term(q2, 0), a3 = term(q3, 0);
+                    const float a4 = term(q4, 0), a5 = term(q5, 0), a6 = term(q6, 0), a7 = term(q7, 0);
+                    add(a0, 0);
+                    add(a1, 0);
+                    add(a2, 0);
+                    add(a3, 0);
+                    add(a4, 0);
+                    add(a5, 0);
+                    add(a6, 0);
+                    add(a7, 0);
+                }
             }
             for (; c + 3 * LANES < cnt; c += 4 * LANES) {
                 const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
-                const float a0 = term(q0), a1 = term(q1), a2 = term(q2), a3 = term(q3);
-                add(a0);
-                add(a1);
-                add(a2);
-                add(a3);
+                float a[NP][4];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    a[i][0] = term(q0, i);
+                    a[i][1] = term(q1, i);
+                    a[i][2] = term(q2, i);
+                    a[i][3] = term(q3, i);
+                }
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    add(a[i][0], i);
+                    add(a[i][1], i);
+                    add(a[i][2], i);
+                    add(a[i][3], i);
+                }
             }
-            for (; c < cnt; c += LANES) add(term(wob[c]));
+            for (; c < cnt; c += LANES) {
+                const float4 q = wob[c];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) add(term(q, i), i);
+            }
         };
         // Fills list entries [cnt, padded) with far-away padding so that
         // the scoring loop runs only whole groups of four independent terms
@@ -349,17 +376,28 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
         };
         bool have = false;
         if (reuse && wl.n >= 0) {
-            const bool in = px >= wl.lx && px <= wl.hx && py >= wl.ly && py <= wl.hy && pz >= wl.lz && pz <= wl.hz;
+            bool in = true;
+#pragma unroll
+            for (int i = 0; i < NP; ++i)
+                in = in && px[i] >= wl.lx && px[i] <= wl.hx && py[i] >= wl.ly && py[i] <= wl.hy && pz[i] >= wl.lz &&
+                     pz[i] <= wl.hz;
             have = __all_sync(0xffffffffu, in);
         }
         if (!have) {
-            const unsigned kx = float_key(px), ky = float_key(py), kz = float_key(pz);
-            const float lox = key_float(__reduce_min_sync(0xffffffffu, kx));
-            const float hix = key_float(__reduce_max_sync(0xffffffffu, kx));
-            const float loy = key_float(__reduce_min_sync(0xffffffffu, ky));
-            const float hiy = key_float(__reduce_max_sync(0xffffffffu, ky));
-            const float loz = key_float(__reduce_min_sync(0xffffffffu, kz));
-            const float hiz = key_float(__reduce_max_sync(0xffffffffu, kz));
+            unsigned kxl = float_key(px[0]), kyl = float_key(py[0]), kzl = float_key(pz[0]);
+            unsigned kxh = kxl, kyh = kyl, kzh = kzl;
+#pragma unroll
+            for (int i = 1; i < NP; ++i) {
+                const unsigned kx = float_key(px[i]), ky = float_key(py[i]), kz = float_key(pz[i]);
+                kxl = min(kxl, kx); kyl = min(kyl, ky); kzl = min(kzl, kz);
+                kxh = max(kxh, kx); kyh = max(kyh, ky); kzh = max(kzh, kz);
+            }
+            const float lox = key_float(__reduce_min_sync(0xffffffffu, kxl));
+            const float hix = key_float(__reduce_max_sync(0xffffffffu, kxh));
+            const float loy = key_float(__reduce_min_sync(0xffffffffu, kyl));
+            const float hiy = key_float(__reduce_max_sync(0xffffffffu, kyh));
+            const float loz = key_float(__reduce_min_sync(0xffffffffu, kzl));
+            const float hiz = key_float(__reduce_max_sync(0xffffffffu, kzh));
             // Test box: the warp's box, enlarged by the margin while a list
             // is being built.
             const bool build = wl.n != -2;
@@ -409,7 +447,7 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
                 if (fits) {
                     base += cnt;
                 } else {
-                    *kept_out += (unsigned)cnt;
+                    *kept_out += (unsigned)(NP * cnt);
                     score(pad(cnt));
                     __syncwarp();
                 }
@@ -423,22 +461,38 @@ __device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float
             }
         }
         if (have) {
-            *kept_out += (unsigned)wl.n;
+            *kept_out += (unsigned)(NP * wl.n);
             score(wl.np);
             __syncwarp();
         }
     }
-    if (LANES > 1) {
-        unsigned h = hit ? 1u : 0u;
 #pragma unroll
-        for (int off = LANES / 2; off > 0; off >>= 1) {
-            bar += __shfl_xor_sync(0xffffffffu, bar, off, LANES);
-            h |= __shfl_xor_sync(0xffffffffu, h, off, LANES);
+    for (int i = 0; i < NP; ++i) {
+        if (LANES > 1) {
+            unsigned h = hit[i] ? 1u : 0u;
+#pragma unroll
+            for (int off = LANES / 2; off > 0; off >>= 1) {
+                bar[i] += __shfl_xor_sync(0xffffffffu, bar[i], off, LANES);
+                h |= __shfl_xor_sync(0xffffffffu, h, off, LANES);
+            }
+            hit[i] = h != 0u;
         }
-        hit = h != 0u;
+        hit_out[i] = hit[i];
+        bar_out[i] = C.c_bar * bar[i];
     }
-    *hit_out = hit;
-    return C.c_bar * bar;
+}
+
+// One position (see obstacle_cost_n).
+template <int LANES>
+__device__ __forceinline__ float obstacle_cost(const DevCost& C, float px, float py, float pz, const float4* so,
+                                               int M, int lane, int wlane, float4* wob, WarpList& wl,
+                                               float margin, bool reuse, bool* hit_out, unsigned* kept_out) {
+    const float x[1] = {px}, y[1] = {py}, z[1] = {pz};
+    float b[1];
+    bool h[1];
+    obstacle_cost_n<LANES, 1>(C, x, y, z, so, M, lane, wlane, wob, wl, margin, reuse, b, h, kept_out);
+    *hit_out = h[0];
+    return b[0];
 }
 
 // Grid-based collision module: is world position (wx, wy, wz) inside an
@@ -849,7 +903,44 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                                                           cull_margin, reuse_lists, &hit, &kept));
                 if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
                 nhit += hit ? 1 : 0;
-                for (int j = 0; j < N; ++j) {
+                int j = 0;
+                if (reuse_lists && M > 0) {
+                    // Two states per pass over the kept list: the scoring is
+                    // latency-bound, and two positions give each loaded
+                    // obstacle twice the independent work.  The sums are
+                    // bitwise those of one state at a time (terms below
+                    // the floor are 0 whichever box kept their obstacle).
+                    for (; j + 1 < N; j += 2) {
+                        const unsigned g0 = g_run + (unsigned)j, g1 = g0 + 1u;
+                        const int s0 = slot_of(g0), s1 = slot_of(g1);
+                        const bool ok0 = mbar_wait_or_abort(bar_of(s0, X_FULL), (g0 / kRing) & 1u, abort_flag,
+                                                            wait_polls);
+                        const bool ok1 = ok0 && mbar_wait_or_abort(bar_of(s1, X_FULL), (g1 / kRing) & 1u,
+                                                                   abort_flag, wait_polls);
+                        const float4* xr0 = xring + 2 * ring_idx(s0);
+                        const float4* xr1 = xring + 2 * ring_idx(s1);
+                        const float4 a0 = xr0[0], a1 = xr0[1], b0 = xr1[0], b1 = xr1[1];
+                        mbar_arrive(bar_of(s0, X_EMPTY));
+                        mbar_arrive(bar_of(s1, X_EMPTY));
+                        // Compensated positions of the two states.
+                        const float qx[2] = {a0.x - a1.x, b0.x - b1.x};
+                        const float qy[2] = {a0.y - a1.y, b0.y - b1.y};
+                        const float qz[2] = {a0.z - a1.z, b0.z - b1.z};
+                        float bars[2];
+                        bool hits[2];
+                        obstacle_cost_n<LANES, 2>(C, qx, qy, qz, sobs, M, lane, wlane, wob, wl, cull_margin, true,
+                                                  bars, hits, &kept);
+                        const float st[2] = {(ok0 ? a0.w : NAN) + bars[0], (ok1 ? b0.w : NAN) + bars[1]};
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            bool h = hits[i];
+                            if (C.grid) h |= grid_hit(C, qx[i] + p0x, qy[i] + p0y, qz[i] + p0z);
+                            nhit += h ? 1 : 0;
+                            kahan_add(S, Sc, st[i]);
+                        }
+                    }
+                }
+                for (; j < N; ++j) {
                     const unsigned g = g_run + (unsigned)j;
                     const int slot = slot_of(g);
                     const unsigned ph = (g / kRing) & 1u;
