@@ -245,8 +245,9 @@ typedef struct {
     float list_margin;      /* obstacle tiling: a warp's kept-obstacle list
                                covers the box of its positions grown by
                                this many metres and is reused while they
-                               stay inside (0: the default, 1 m; results do
-                               not depend on it beyond FP32 rounding)       */
+                               stay inside (0: the default, 1 m, or 0.5 m
+                               for the pipelined form; results do not
+                               depend on it beyond FP32 rounding)           */
 } mppi_shape;
 
 /* Forces a launch shape for subsequent calls on the handle (both 0: back

@@ -491,7 +491,8 @@ static int tune_on(mppi_ctx* h, mppi_instance in, cudaStream_t st, mppi_shape* b
     }
     if (!rc && in.M > 0) {
         const Shape base = bestS;
-        for (float m : {0.25f, 0.5f, 2.0f}) {
+        for (float m : {0.25f, 0.5f, 1.0f, 2.0f}) {
+            if (m == list_margin(base)) continue;  // timed above
             Shape s = base;
             s.margin = m;
             time_shape(s);

@@ -36,7 +36,10 @@ struct DevModel {
 // A warp's kept-obstacle list is built for the warp's position box grown by
 // this margin on every side and reused while all of the warp's positions stay
 // inside; a larger margin means fewer rebuilds but more (exactly zero) terms.
-constexpr float kCullMargin = 1.0f;  // [m]
+// The pipelined form, whose cost lanes wait on the list, is faster with the
+// smaller margin (closed-loop step, 64 spheres: 91 against 93 us).
+constexpr float kCullMargin = 1.0f;           // [m]
+constexpr float kCullMarginPipelined = 0.5f;  // [m]
 
 // Floor of the obstacle barrier: a term exp(-beta max(s, 0)) below
 // 2^-kBarrierFloorLog2 counts as exactly zero.  Per obstacle and state that
@@ -87,10 +90,12 @@ struct Shape {
     int block;     // threads per block
     int lanes;     // lanes per sample
     int pipe;      // 1: pipelined (a dynamics thread and a cost thread per sample)
-    float margin;  // kept-obstacle list margin [m]; 0: kCullMargin
+    float margin;  // kept-obstacle list margin [m]; 0: the default of the form
 };
 
-inline float list_margin(const Shape& s) { return s.margin > 0.0f ? s.margin : kCullMargin; }
+inline float list_margin(const Shape& s) {
+    return s.margin > 0.0f ? s.margin : s.pipe ? kCullMarginPipelined : kCullMargin;
+}
 
 // Everything one launch of the fused kernel needs.
 struct LaunchArgs {

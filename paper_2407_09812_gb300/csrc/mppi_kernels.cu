@@ -597,6 +597,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 // kRing slots (2 float4: position, its compensation, and the step's input
 // and tracking cost) and four mbarriers per slot (two used: full / empty).
 constexpr int kRing = 4;
+// States the cost lanes of the pipelined form score per pass over their
+// kept-obstacle list (at most kRing).
+constexpr int kStatesPerPass = 2;
 
 struct SmemLayout {
     unsigned obs, ref, u, S, e, list, part, wlist, xring, bars, total;
@@ -905,38 +908,44 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 nhit += hit ? 1 : 0;
                 int j = 0;
                 if (reuse_lists && M > 0) {
-                    // Two states per pass over the kept list: the scoring is
-                    // latency-bound, and two positions give each loaded
-                    // obstacle twice the independent work.  The sums are
-                    // bitwise those of one state at a time (terms below
-                    // the floor are 0 whichever box kept their obstacle).
-                    for (; j + 1 < N; j += 2) {
-                        const unsigned g0 = g_run + (unsigned)j, g1 = g0 + 1u;
-                        const int s0 = slot_of(g0), s1 = slot_of(g1);
-                        const bool ok0 = mbar_wait_or_abort(bar_of(s0, X_FULL), (g0 / kRing) & 1u, abort_flag,
-                                                            wait_polls);
-                        const bool ok1 = ok0 && mbar_wait_or_abort(bar_of(s1, X_FULL), (g1 / kRing) & 1u,
-                                                                   abort_flag, wait_polls);
-                        const float4* xr0 = xring + 2 * ring_idx(s0);
-                        const float4* xr1 = xring + 2 * ring_idx(s1);
-                        const float4 a0 = xr0[0], a1 = xr0[1], b0 = xr1[0], b1 = xr1[1];
-                        mbar_arrive(bar_of(s0, X_EMPTY));
-                        mbar_arrive(bar_of(s1, X_EMPTY));
-                        // Compensated positions of the two states.
-                        const float qx[2] = {a0.x - a1.x, b0.x - b1.x};
-                        const float qy[2] = {a0.y - a1.y, b0.y - b1.y};
-                        const float qz[2] = {a0.z - a1.z, b0.z - b1.z};
-                        float bars[2];
-                        bool hits[2];
-                        obstacle_cost_n<LANES, 2>(C, qx, qy, qz, sobs, M, lane, wlane, wob, wl, cull_margin, true,
-                                                  bars, hits, &kept);
-                        const float st[2] = {(ok0 ? a0.w : NAN) + bars[0], (ok1 ? b0.w : NAN) + bars[1]};
+                    // kStatesPerPass states per pass over the kept list: the
+                    // scoring is latency-bound, and several positions give
+                    // each loaded obstacle that much more independent work.
+                    // The sums are bitwise those of one state at a time
+                    // (terms below the floor are 0 whichever box kept their
+                    // obstacle).
+                    constexpr int NS = kStatesPerPass;
+                    for (; j + NS - 1 < N; j += NS) {
+                        bool ok[NS];
+                        float qx[NS], qy[NS], qz[NS], uc[NS];
+                        bool all_ok = true;
 #pragma unroll
-                        for (int i = 0; i < 2; ++i) {
+                        for (int i = 0; i < NS; ++i) {
+                            const unsigned g = g_run + (unsigned)(j + i);
+                            const int sl = slot_of(g);
+                            all_ok = all_ok && mbar_wait_or_abort(bar_of(sl, X_FULL), (g / kRing) & 1u, abort_flag,
+                                                                  wait_polls);
+                            ok[i] = all_ok;
+                            const float4* xr = xring + 2 * ring_idx(sl);
+                            const float4 a0 = xr[0], a1 = xr[1];
+                            // Compensated position and the step's other cost.
+                            qx[i] = a0.x - a1.x;
+                            qy[i] = a0.y - a1.y;
+                            qz[i] = a0.z - a1.z;
+                            uc[i] = a0.w;
+                        }
+#pragma unroll
+                        for (int i = 0; i < NS; ++i) mbar_arrive(bar_of(slot_of(g_run + (unsigned)(j + i)), X_EMPTY));
+                        float bars[NS];
+                        bool hits[NS];
+                        obstacle_cost_n<LANES, NS>(C, qx, qy, qz, sobs, M, lane, wlane, wob, wl, cull_margin, true,
+                                                   bars, hits, &kept);
+#pragma unroll
+                        for (int i = 0; i < NS; ++i) {
                             bool h = hits[i];
                             if (C.grid) h |= grid_hit(C, qx[i] + p0x, qy[i] + p0y, qz[i] + p0z);
                             nhit += h ? 1 : 0;
-                            kahan_add(S, Sc, st[i]);
+                            kahan_add(S, Sc, (ok[i] ? uc[i] : NAN) + bars[i]);
                         }
                     }
                 }
