@@ -216,6 +216,17 @@ __device__ __forceinline__ Feasible feasible(const DevModel& M, const State& s, 
 
 // ------------------------------------------------------------------- cost
 
+// Input and input-change cost of one step (Eq. cost): ||u_j||^2_R and, from
+// the second step on, ||u_j - u_{j-1}||^2_{R_Delta}.
+__device__ __forceinline__ float input_cost(const DevCost& C, const float4 u, const float4 u_prev, bool rate) {
+    float c = fmaf(C.R[0], u.x * u.x, fmaf(C.R[1], u.y * u.y, fmaf(C.R[2], u.z * u.z, C.R[3] * u.w * u.w)));
+    if (rate) {
+        const float ex = u.x - u_prev.x, ey = u.y - u_prev.y, ez = u.z - u_prev.z, ew = u.w - u_prev.w;
+        c += fmaf(C.Rd[0], ex * ex, fmaf(C.Rd[1], ey * ey, fmaf(C.Rd[2], ez * ez, C.Rd[3] * ew * ew)));
+    }
+    return c;
+}
+
 // rho_ref of Sec. IV-C against one padded reference row (16 floats).
 // The compensation terms c hold minus the low-order parts of p and v.
 __device__ __forceinline__ float tracking_cost(const DevCost& C, const State& x, const Comp& c, const float4* row) {
@@ -594,9 +605,11 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Dynamic shared memory layout (byte offsets), identical on host and device.
 // The pipelined variant adds, per pair of (dynamics, cost) warps, a ring of
-// kRing slots (2 float4: position, its compensation, and the step's input
-// and tracking cost) and four mbarriers per slot (two used: full / empty).
+// kRing slots (kSlotF4 float4 per lane, stored lane-contiguous: the position
+// and the step's tracking cost, the position's compensation terms, and the
+// control) and four mbarriers per slot (two used: full / empty).
 constexpr int kRing = 4;
+constexpr int kSlotF4 = 3;
 // States the cost lanes of the pipelined form score per pass over their
 // kept-obstacle list (at most kRing).
 constexpr int kStatesPerPass = 2;
@@ -621,7 +634,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.list = o; o = align_up(o + 4u * (unsigned)spb, 128);
     L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
     L.wlist = o; o = align_up(o + 32u * (unsigned)block, 128);  // 64 float4 per warp
-    L.xring = o; o = align_up(o + 32u * slots, 128);
+    L.xring = o; o = align_up(o + 16u * kSlotF4 * slots, 128);
     L.bars = o;  o = align_up(o + 8u * 4u * (slots / 32u), 128);
     L.total = o;
     return L;
@@ -809,11 +822,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 const float4 un = su[j];
                 const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
                                                               __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
-                float step = fmaf(C.R[0], u.x * u.x, fmaf(C.R[1], u.y * u.y, fmaf(C.R[2], u.z * u.z, C.R[3] * u.w * u.w)));
-                if (j > 0) {
-                    const float ex = u.x - u_prev.x, ey = u.y - u_prev.y, ez = u.z - u_prev.z, ew = u.w - u_prev.w;
-                    step += fmaf(C.Rd[0], ex * ex, fmaf(C.Rd[1], ey * ey, fmaf(C.Rd[2], ez * ez, C.Rd[3] * ew * ew)));
-                }
+                float step = input_cost(C, u, u_prev, j > 0);
                 u_prev = u;
                 const Feasible f = feasible(Mdl, x, u, inv_dt);
                 rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
@@ -852,7 +861,8 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             volatile int* abort_flag = &s_abort;
             auto slot_of = [&](unsigned g) { return (int)(g % kRing); };
             auto bar_of = [&](int slot, int kind) { return bars + 8u * (unsigned)((pw * kRing + slot) * 4 + kind); };
-            auto ring_idx = [&](int slot) { return (pw * kRing + slot) * 32 + (group & 31); };
+            // Field f of this lane's entry in a ring slot.
+            auto ring_at = [&](int slot, int f) { return xring + ((pw * kRing + slot) * kSlotF4 + f) * 32 + (group & 31); };
             constexpr int X_FULL = 2, X_EMPTY = 3;
             const int k_raw = tile * spb + group;
             const bool valid = k_raw < K;
@@ -863,7 +873,6 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             x.wx = s_x0[10]; x.wy = s_x0[11]; x.wz = s_x0[12];
             Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (!is_cost) {
-                float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
                 float4 d_next = noise_delta(normals4(k, 0u, iter, key0, key1), sigma);
                 for (int j = 0; j < N; ++j) {
                     const unsigned g = g_run + (unsigned)j;
@@ -874,23 +883,16 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                     const float4 un = su[j];
                     const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
                                                                   __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
-                    float ucost = fmaf(C.R[0], u.x * u.x,
-                                       fmaf(C.R[1], u.y * u.y, fmaf(C.R[2], u.z * u.z, C.R[3] * u.w * u.w)));
-                    if (j > 0) {
-                        const float ex = u.x - u_prev.x, ey = u.y - u_prev.y, ez = u.z - u_prev.z,
-                                    ew = u.w - u_prev.w;
-                        ucost += fmaf(C.Rd[0], ex * ex, fmaf(C.Rd[1], ey * ey, fmaf(C.Rd[2], ez * ez, C.Rd[3] * ew * ew)));
-                    }
-                    u_prev = u;
                     const Feasible f = feasible(Mdl, x, u, inv_dt);
                     rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
-                    // Input, input-change and tracking cost of the step, in
-                    // the same order as the one-thread form.
-                    ucost += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
+                    // The tracking cost is formed here; the input and
+                    // input-change cost by the cost lanes, from the control
+                    // handed over with the position.
+                    const float tcost = tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
                     if (g >= (unsigned)kRing) mbar_wait_or_abort(bar_of(slot, X_EMPTY), ph ^ 1u, abort_flag, wait_polls);
-                    float4* xs = xring + 2 * ring_idx(slot);
-                    xs[0] = make_float4(x.px, x.py, x.pz, ucost);
-                    xs[1] = make_float4(cmp.px, cmp.py, cmp.pz, 0.0f);
+                    *ring_at(slot, 0) = make_float4(x.px, x.py, x.pz, tcost);
+                    *ring_at(slot, 1) = make_float4(cmp.px, cmp.py, cmp.pz, 0.0f);
+                    *ring_at(slot, 2) = u;
                     mbar_arrive(bar_of(slot, X_FULL));
                 }
             } else {
@@ -906,6 +908,21 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                                                           cull_margin, reuse_lists, &hit, &kept));
                 if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
                 nhit += hit ? 1 : 0;
+                // Reads what was handed over for step j + 1 (slot sl):
+                // returns the compensated position and the step's input,
+                // input-change and tracking cost, in the one-thread form's
+                // order.
+                float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+                auto take = [&](int sl, int jj, float& qpx, float& qpy, float& qpz) -> float {
+                    const float4 r0 = *ring_at(sl, 0), r1 = *ring_at(sl, 1), u = *ring_at(sl, 2);
+                    float c = input_cost(C, u, u_prev, jj > 0);
+                    u_prev = u;
+                    c += r0.w;
+                    qpx = r0.x - r1.x;
+                    qpy = r0.y - r1.y;
+                    qpz = r0.z - r1.z;
+                    return c;
+                };
                 int j = 0;
                 if (reuse_lists && M > 0) {
                     // kStatesPerPass states per pass over the kept list: the
@@ -926,13 +943,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                             all_ok = all_ok && mbar_wait_or_abort(bar_of(sl, X_FULL), (g / kRing) & 1u, abort_flag,
                                                                   wait_polls);
                             ok[i] = all_ok;
-                            const float4* xr = xring + 2 * ring_idx(sl);
-                            const float4 a0 = xr[0], a1 = xr[1];
-                            // Compensated position and the step's other cost.
-                            qx[i] = a0.x - a1.x;
-                            qy[i] = a0.y - a1.y;
-                            qz[i] = a0.z - a1.z;
-                            uc[i] = a0.w;
+                            uc[i] = take(sl, j + i, qx[i], qy[i], qz[i]);
                         }
 #pragma unroll
                         for (int i = 0; i < NS; ++i) mbar_arrive(bar_of(slot_of(g_run + (unsigned)(j + i)), X_EMPTY));
@@ -954,11 +965,10 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                     const int slot = slot_of(g);
                     const unsigned ph = (g / kRing) & 1u;
                     const bool ok = mbar_wait_or_abort(bar_of(slot, X_FULL), ph, abort_flag, wait_polls);
-                    const float4* xr = xring + 2 * ring_idx(slot);
-                    const float4 a0 = xr[0], a1 = xr[1];
+                    float qpx, qpy, qpz;  // compensated position
+                    const float uc = take(slot, j, qpx, qpy, qpz);
                     mbar_arrive(bar_of(slot, X_EMPTY));
-                    const float qpx = a0.x - a1.x, qpy = a0.y - a1.y, qpz = a0.z - a1.z;  // compensated position
-                    float step = ok ? a0.w : NAN;
+                    float step = ok ? uc : NAN;
                     step += obstacle_cost<LANES>(C, qpx, qpy, qpz, sobs, M, lane, wlane, wob, wl, cull_margin,
                                                  reuse_lists, &hit, &kept);
                     if (C.grid) hit |= grid_hit(C, qpx + p0x, qpy + p0y, qpz + p0z);
