@@ -210,6 +210,35 @@ def _obstacle_count(obs) -> int:
     return n // 4
 
 
+class _AddressCache:
+    """Host addresses of arrays the binding has seen, by identity.
+
+    `ndarray.ctypes.data` costs about a microsecond per call, several times
+    per solve.  A closed loop passes the same arrays again (its obstacle
+    set) or the arrays a previous solve returned (the next state and
+    nominal), whose addresses are known when they are made.  An entry keeps
+    its array alive, so its id cannot be reused by another object and its
+    data cannot be reallocated (resize refuses a referenced array); the
+    cache holds the last few entries only."""
+
+    def __init__(self, size: int = 16):
+        self.size = size
+        self.d = {}
+
+    def add(self, a, addr: int) -> int:
+        d = self.d
+        if len(d) >= self.size:
+            d.pop(next(iter(d)))
+        d[id(a)] = (a, addr)
+        return addr
+
+    def get(self, a) -> int:
+        e = self.d.get(id(a))
+        if e is not None and e[0] is a:
+            return e[1]
+        return self.add(a, a.ctypes.data)
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch
@@ -232,6 +261,8 @@ class Solver:
         _check(lib().mppi_create(C.byref(self._m), C.byref(self._p), C.byref(cap) if cap else None, C.byref(h)),
                "mppi_create")
         self.h = h
+        self._addr = _AddressCache()
+        self._blk_t = {}  # ctypes array type per output block size
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:
@@ -286,16 +317,26 @@ class Solver:
             _obstacle_count(o)
             _check_sizes(K, N, {"x_hat": x, "ref": r, "u_nom": u})
         o = o.reshape(-1, 4)
-        # One allocation for all outputs (each returned array is its own view).
+        # One allocation for all outputs (each returned array is its own
+        # view); a ctypes array gives its address without an ndarray.ctypes
+        # object.
         n_out = 8 * N + 17 + (K if want_costs else 0)
-        blk = np.empty(n_out, np.float32)
-        base = blk.ctypes.data
+        T = self._blk_t.get(n_out)
+        if T is None:
+            T = self._blk_t[n_out] = C.c_float * n_out
+        buf = T()
+        base = C.addressof(buf)
+        blk = np.frombuffer(buf, np.float32)
         out = {"u_out": blk[:4 * N].reshape(N, 4), "u_cmd": blk[4 * N:4 * N + 4],
                "u_next": blk[4 * N + 4:8 * N + 4].reshape(N, 4), "x_next": blk[8 * N + 4:8 * N + 17],
                "costs": blk[8 * N + 17:] if want_costs else None}
-        rc = lib().mppi_solve(self.h, x.ctypes.data, r.ctypes.data, o.ctypes.data if o.size else None, o.shape[0],
-                              u.ctypes.data, int(it), base, base + 16 * N, base + 16 * N + 16, base + 32 * N + 16,
+        A = self._addr
+        rc = lib().mppi_solve(self.h, A.get(x), A.get(r), A.get(o) if o.size else None, o.shape[0], A.get(u),
+                              int(it), base, base + 16 * N, base + 16 * N + 16, base + 32 * N + 16,
                               base + 32 * N + 68 if want_costs else None)
+        # The next state and nominal are usually the next call's inputs.
+        A.add(out["u_next"], base + 16 * N + 16)
+        A.add(out["x_next"], base + 32 * N + 16)
         if rc not in (OK, ENONFINITE):
             raise MppiError(rc, "mppi_solve")
         out["status"] = rc

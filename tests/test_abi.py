@@ -153,3 +153,23 @@ def test_binding_refuses_buffers_that_do_not_match_the_step(built):
     assert mppi._obstacle_count(None) == 0 and mppi._obstacle_count(np.zeros((5, 4))) == 5
     with pytest.raises(ValueError):
         mppi._obstacle_count(np.zeros(9))
+
+
+def test_binding_address_cache_is_by_identity_and_bounded(built):
+    """The host-buffer binding remembers the addresses of arrays it has
+    seen (or made) by identity; an entry keeps its array alive, so a cached
+    id always names the same array, and only the last few are kept."""
+    import numpy as np
+    from paper_2407_09812_gb300 import mppi
+    c = mppi._AddressCache(4)
+    a = np.arange(8, dtype=np.float32)
+    assert c.get(a) == a.ctypes.data
+    v = a[2:]  # a view: its own object, its own address
+    assert c.get(v) == a.ctypes.data + 8
+    assert c.add(a[1:], a.ctypes.data + 4) == a.ctypes.data + 4
+    others = [np.zeros(3, np.float32) for _ in range(6)]
+    for o in others:
+        assert c.get(o) == o.ctypes.data
+    assert len(c.d) <= 4
+    assert all(e[0] is not a for e in c.d.values())  # evicted in insertion order
+    assert c.get(a) == a.ctypes.data
