@@ -321,3 +321,32 @@ def test_paper_operating_point(M, orc, inp, table1_vehicle):
     for it in range(3):
         p = dict(prob, iter=it)
         assert_step_close(p, gpu_solve(M, p), orc.mppi_step(p, n_threads=8))
+
+
+@pytest.mark.parametrize("log2_term", [-20.0, -40.0, -47.0, -49.0, -60.0])
+def test_barrier_floor(M, orc, inp, log2_term):
+    """Reading R28: a barrier term below 2^-48 counts as 0 on the GPU.  With
+    every other cost weight and the noise at zero, a sample's cost is the
+    barrier sum alone: one sphere is placed so that the hovering states see
+    exp(-beta s) = 2^log2_term.  Above the floor the GPU matches the FP64
+    oracle; below it the GPU's cost is exactly 0 while the oracle's is the
+    (N+1) c_bar 2^log2_term the floor drops."""
+    import math
+    N = 10
+    prob = inp.plain_hover(K=64, N=N, c_p=0.0, c_q=0.0, c_v=0.0, c_w=0.0, R=(0.0,) * 4, Rd=(0.0,) * 4,
+                           sigma=(0.0,) * 4)
+    p = prob["params"]
+    beta, reach = p["beta"], 0.5 + p["r_uav"]
+    s_gap = -log2_term / (beta * math.log2(math.e))  # exp(-beta s) = 2^log2_term
+    d = math.sqrt(reach * reach + s_gap)
+    x0 = prob["x_hat"][0:3].astype(np.float64)
+    prob["obstacles"] = np.array([[x0[0] + d, x0[1], x0[2], 0.5]], np.float32)
+    g = gpu_solve(M, prob)
+    o = orc.mppi_step(prob, n_threads=8)
+    expect = (N + 1) * p["c_bar"] * 2.0 ** log2_term
+    assert np.allclose(o["costs"], expect, rtol=1e-4)  # the placement is what it says
+    if log2_term >= -48.0:
+        assert np.allclose(g["costs"], o["costs"], rtol=1e-4)
+    else:
+        assert np.all(g["costs"] == 0.0)
+        assert np.all(o["costs"] > 0.0) and np.all(o["costs"] <= (N + 1) * p["c_bar"] * 2.0 ** -48)
