@@ -848,12 +848,13 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             // Pipelined rollout.  The dynamics thread of a sample draws the
             // noise (one step ahead, overlapping the RK4 chain), clamps the
             // control, runs the constraint pipeline and RK4 and forms the
-            // step's input, input-change and tracking cost; it hands the new
-            // position (with its compensation terms) and that cost to the
-            // sample's cost lanes through a ring in shared memory.  The cost
-            // lanes score the positions against the obstacles and the grid
-            // while the dynamics thread is already integrating the next
-            // steps.  Every wait is bounded.
+            // step's tracking cost; it hands the new position (with its
+            // compensation terms), that cost and the control to the sample's
+            // cost lanes through a ring in shared memory.  The cost lanes add
+            // the input and input-change cost and score the positions, two
+            // states per pass, against the obstacles and the grid while the
+            // dynamics thread is already integrating the next steps.  Every
+            // wait is bounded.
             const bool is_cost = tid >= spb;
             const int pw = group >> 5;  // warp pair
             float4* xring = reinterpret_cast<float4*>(smem + L.xring);
