@@ -33,17 +33,31 @@ namespace mppi {
 // ------------------------------------------------------------------ noise
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the multiply/xor
-// network, the key bumped by the Weyl constants after each round.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+// network; round r uses the key (k0 + r W0, k1 + r W1), W the Weyl
+// constants.  The round keys are the same for every sample of an instance,
+// so they are formed once per tile (philox_round_keys) and read from shared
+// memory as five (round 2i, round 2i + 1) pairs.
+constexpr unsigned kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox_round(uint4 c, unsigned k0, unsigned k1) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x);
+    const unsigned lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const unsigned lo1 = 0xCD9E8D57u * c.z;
+    return make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+}
+
+__device__ __forceinline__ uint4 philox_round_keys(unsigned key0, unsigned key1, unsigned i) {
+    return make_uint4(key0 + 2u * i * kPhiloxW0, key1 + 2u * i * kPhiloxW1, key0 + (2u * i + 1u) * kPhiloxW0,
+                      key1 + (2u * i + 1u) * kPhiloxW1);
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint4* rk) {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned hi0 = __umulhi(0xD2511F53u, c.x);
-        const unsigned lo0 = 0xD2511F53u * c.x;
-        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z);
-        const unsigned lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+    for (int i = 0; i < 5; ++i) {
+        const uint4 k = rk[i];
+        c = philox_round(c, k.x, k.y);
+        c = philox_round(c, k.z, k.w);
     }
     return c;
 }
@@ -54,10 +68,9 @@ __device__ __forceinline__ float uniform01(unsigned r) {
 }
 
 // Four standard normals for sample k, step j: Box-Muller on the two
-// uniform pairs of one Philox call.  Counter (k, j, iter), key (key0, key1).
-__device__ __forceinline__ float4 normals4(unsigned k, unsigned j, unsigned long long iter, unsigned key0,
-                                           unsigned key1) {
-    const uint4 r = philox4x32_10(make_uint4(k, j, (unsigned)iter, (unsigned)(iter >> 32)), key0, key1);
+// uniform pairs of one Philox call.  Counter (k, j, iter), round keys rk.
+__device__ __forceinline__ float4 normals4(unsigned k, unsigned j, unsigned long long iter, const uint4* rk) {
+    const uint4 r = philox4x32_10(make_uint4(k, j, (unsigned)iter, (unsigned)(iter >> 32)), rk);
     const float u0 = uniform01(r.x), u1 = uniform01(r.y), u2 = uniform01(r.z), u3 = uniform01(r.w);
     // -2 ln u > 0 for every u of the map (u < 1), so sqrt(x) = x rsqrt(x).
     const float a01 = -2.0f * logf(u0), a23 = -2.0f * logf(u2);
@@ -659,6 +672,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
     __shared__ double s_rho;
     __shared__ double s_redd[32];
     __shared__ float s_red[32];
+    __shared__ uint4 s_rk[5];  // Philox round keys of the tile's instance
 
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
@@ -728,7 +742,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
         const int K = sI.K, N = sI.N, M = sI.M;
         const float dt = sI.dt, inv_dt = 1.0f / sI.dt, lambda = sI.lambda;
         const unsigned long long iter = sI.iter_dev ? *sI.iter_dev : sI.iter;
-        const unsigned key0 = sI.key0, key1 = sI.key1;
+        if (tid < 5) s_rk[tid] = philox_round_keys(sI.key0, sI.key1, (unsigned)tid);
         float sigma[4] = {sI.sigma[0], sI.sigma[1], sI.sigma[2], sI.sigma[3]};
 
         // ---------------------------------- stage inputs in shared memory
@@ -818,7 +832,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             nhit += hit ? 1 : 0;
             float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int j = 0; j < N; ++j) {
-                const float4 d = noise_delta(normals4(k, (unsigned)j, iter, key0, key1), sigma);
+                const float4 d = noise_delta(normals4(k, (unsigned)j, iter, s_rk), sigma);
                 const float4 un = su[j];
                 const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
                                                               __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
@@ -874,13 +888,13 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             x.wx = s_x0[10]; x.wy = s_x0[11]; x.wz = s_x0[12];
             Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (!is_cost) {
-                float4 d_next = noise_delta(normals4(k, 0u, iter, key0, key1), sigma);
+                float4 d_next = noise_delta(normals4(k, 0u, iter, s_rk), sigma);
                 for (int j = 0; j < N; ++j) {
                     const unsigned g = g_run + (unsigned)j;
                     const int slot = slot_of(g);
                     const unsigned ph = (g / kRing) & 1u;
                     const float4 d = d_next;
-                    d_next = noise_delta(normals4(k, (unsigned)min(j + 1, N - 1), iter, key0, key1), sigma);
+                    d_next = noise_delta(normals4(k, (unsigned)min(j + 1, N - 1), iter, s_rk), sigma);
                     const float4 un = su[j];
                     const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
                                                                   __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
@@ -1038,7 +1052,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 for (int ci = grp; ci < count; ci += G) {
                     const int g = slist[ci];
                     const float e = sE[g];
-                    const float4 d = noise_delta(normals4((unsigned)(tile_base + g), (unsigned)j, iter, key0, key1), sigma);
+                    const float4 d = noise_delta(normals4((unsigned)(tile_base + g), (unsigned)j, iter, s_rk), sigma);
                     acc.x = fmaf(e, d.x, acc.x);
                     acc.y = fmaf(e, d.y, acc.y);
                     acc.z = fmaf(e, d.z, acc.z);
