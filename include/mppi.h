@@ -158,7 +158,9 @@ int mppi_set_grid(mppi_handle h, const uint8_t* grid, int32_t nx, int32_t ny, in
  *   x_next[13]   x_hat advanced by the applied command over shift_alpha*dt;
  *   costs[K]     per-sample cost S_k.
  * Returns MPPI_OK, MPPI_EINVAL, MPPI_ECUDA, MPPI_ETIMEOUT, or
- * MPPI_ENONFINITE (every S_k non-finite: u_out = u_nom). */
+ * MPPI_ENONFINITE (every S_k non-finite: u_out = u_nom).  On MPPI_ETIMEOUT
+ * (a bounded device wait gave up) the outputs are written but hold
+ * unspecified values; on MPPI_EINVAL and MPPI_ECUDA they are not written. */
 int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float* obstacles, int32_t M,
                const float* u_nom, uint64_t iter, float* u_out, float* u_cmd, float* u_next,
                float* x_next, float* costs);
