@@ -100,7 +100,9 @@ typedef struct {
     int32_t reserved;  /* must be 0                                         */
 } mppi_params;
 
-/* Capacity of a handle's device workspace. */
+/* Capacity a handle's device workspace is allocated for at creation (a
+ * call that needs more grows it; sizing it up front keeps allocation out of
+ * later calls). */
 typedef struct {
     int32_t max_instances; /* instances per batched launch (>= 1)           */
     int64_t max_samples;   /* sum of K over one batched launch              */
@@ -110,23 +112,30 @@ typedef struct {
 
 typedef struct mppi_ctx* mppi_handle;
 
-/* Library version and the error string of a code (static storage). */
+/* Library version and the error string of a code (static storage; the
+ * paper has no counterpart).  mppi_strerror never returns NULL: unknown
+ * codes give a generic string. */
 const char* mppi_version(void);
 const char* mppi_strerror(int code);
 
-/* Creates a handle for one vehicle model and one parameter set on the
- * current CUDA device; allocates its device workspace for `cap` (NULL:
- * one instance of params->K, params->N, MPPI_M_MAX obstacles).
+/* Creates a handle for one vehicle model (Table I, Sec. III-B) and one
+ * parameter set (the MPPI settings of Table II and the cost of Sec. IV-C/D)
+ * on the current CUDA device; allocates its device workspace for `cap`
+ * (NULL: one instance of params->K, params->N, MPPI_M_MAX obstacles).
+ * *out is set to NULL on any error.
  * Returns MPPI_EINVAL for non-finite or out-of-range values, MPPI_ENOMEM
  * or MPPI_ECUDA if the workspace cannot be allocated. */
 int mppi_create(const mppi_model* model, const mppi_params* params, const mppi_capacity* cap,
                 mppi_handle* out);
 
-/* Frees the handle and its workspace (synchronises its device work). */
+/* Frees the handle and its workspace (synchronises its device work; the
+ * paper has no counterpart).  NULL is ignored. */
 void mppi_destroy(mppi_handle h);
 
-/* Replaces the parameter set (K and N within the capacity).  Takes effect
- * for calls made afterwards. */
+/* Replaces the parameter set (Table II settings and cost weights).  Takes
+ * effect for calls made afterwards; cached graphs are dropped, and the
+ * workspace grows on the next call if K or N exceed what it holds.
+ * MPPI_EINVAL (nothing changed) for invalid values. */
 int mppi_set_params(mppi_handle h, const mppi_params* params);
 
 /* Grid-based collision module (Sec. IV-D names occupancy maps as one way
@@ -165,8 +174,11 @@ int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float*
                const float* u_nom, uint64_t iter, float* u_out, float* u_cmd, float* u_next,
                float* x_next, float* costs);
 
-/* The same step with DEVICE buffers, enqueued on `stream` (a cudaStream_t;
- * NULL = legacy default stream); returns after enqueueing.  `status`
+/* The same step (Alg. 1, body of the loop) with DEVICE buffers, enqueued
+ * on `stream` (a cudaStream_t; NULL = legacy default stream); returns
+ * after enqueueing.  Buffer sizes and layouts as for mppi_solve; x_hat,
+ * ref, u_nom, the outputs and costs must be 4-byte aligned and obstacles
+ * 16-byte aligned (MPPI_EINVAL otherwise).  `status`
  * (device int32, may be NULL) receives the step's result code.  All input
  * buffers must stay valid and unchanged until the stream reaches the end
  * of the step.  Graph capture of the stream is allowed. */
@@ -201,8 +213,9 @@ typedef struct {
     int32_t reserved;   /* must be 0                                        */
 } mppi_instance;
 
-/* Many independent MPPI steps of uneven (K, N, M) in one persistent launch
- * on `stream` (the batched form of mppi_solve_async).  `instances` is a
+/* Many independent MPPI steps (Alg. 1, one per vehicle) of uneven
+ * (K, N, M) in one persistent launch on `stream` (the batched form of
+ * mppi_solve_async; batching is this library's, not the paper's).  `instances` is a
  * HOST array of n descriptors (copied before return).  The launch shape
  * (block size, samples per warp) is taken from the handle's tuning table
  * (mppi_autotune) or a default.  Every instance's result equals what
@@ -253,10 +266,11 @@ typedef struct {
 } mppi_shape;
 
 /* Forces a launch shape for subsequent calls on the handle (both 0: back
- * to the tuned/default choice). */
+ * to the tuned/default choice; the paper has no counterpart).
+ * MPPI_EINVAL for an unsupported shape or margin. */
 int mppi_set_shape(mppi_handle h, const mppi_shape* shape);
 
-/* Project autotuner: times every candidate shape (block size, samples per
+/* Project autotuner (the paper has no counterpart): times every candidate shape (block size, samples per
  * warp, pipelined form, then the obstacle tiling of the fastest) on a
  * synthetic problem of size (K, N, M) on `stream`, stores the fastest in
  * the handle's table for that size bucket and returns it in *best (may be
@@ -270,7 +284,8 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
  * relative to the rollouts, which a synthetic problem does not reproduce. */
 int mppi_autotune_instance(mppi_handle h, const mppi_instance* instance, mppi_shape* best, void* stream);
 
-/* Looks up the shape the handle uses for a problem of size (K, N, M). */
+/* Looks up the shape the handle uses for a problem of size (K, N, M)
+ * (the paper has no counterpart). */
 int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* shape);
 
 /* ---------------------------------------------------------------------
@@ -316,7 +331,12 @@ typedef struct {
     double busy_us;            /* sum over batches of launch-to-completion time */
 } mppi_server_stats;
 
-/* Creates a server on the current device for one vehicle model and one set
+/* Serving (the paper runs one controller per vehicle; continuous batching
+ * of many vehicles' solves is this library's).  Every request is one
+ * Alg. 1 step of its vehicle with the warm start and Philox counter kept
+ * on the device.
+ *
+ * Creates a server on the current device for one vehicle model and one set
  * of cost weights and options (params' K, N, dt, lambda, sigma, seed are
  * unused: they are per vehicle).  MPPI_ENOMEM if the slots' workspaces do
  * not fit the budget. */
@@ -344,7 +364,8 @@ int mppi_server_remove_vehicle(mppi_server* s, int32_t vehicle_id);
 int mppi_server_submit(mppi_server* s, int32_t vehicle_id, const float* x_hat, const float* ref,
                        uint64_t* request_id);
 
-/* Moves up to `max` completed results into out[] and sets *n. */
+/* Moves up to `max` completed results into out[] (caller-owned, room for
+ * `max`) and sets *n; MPPI_EINVAL for a NULL n or a NULL out with max > 0. */
 int mppi_server_poll(mppi_server* s, mppi_result* out, int32_t max, int32_t* n);
 
 /* Waits until no request is queued or in flight (timeout_ms < 0: no
@@ -357,6 +378,8 @@ int mppi_server_drain(mppi_server* s, int32_t timeout_ms);
 int mppi_server_export_vehicle(mppi_server* s, int32_t vehicle_id, float* u_nom, uint64_t* iter);
 int mppi_server_import_vehicle(mppi_server* s, int32_t vehicle_id, const float* u_nom, uint64_t iter);
 
+/* Copies the server's counters (submitted, completed, rejected, batches,
+ * device bytes in use and budgeted, busy time) into *st. */
 int mppi_server_get_stats(mppi_server* s, mppi_server_stats* st);
 
 /* Stops the dispatcher after draining and frees everything. */
