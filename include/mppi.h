@@ -395,9 +395,13 @@ int mppi_server_destroy(mppi_server* s);
  * the library (about 1 MiB, held by every GPU that loads the library until
  * the process exits), so sizes are limited to K <= 32768 and N <= 256
  * (MPPI_EINVAL beyond).  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  All
- * calls share the array: calls whose work overlaps on the GPU race, so
- * order them on one stream.  Launch shape: 128 threads, one per sample. */
+ * device address; make that first call before any stream capture.  The
+ * address is kept for the life of the process: do not call this entry
+ * point again after cudaDeviceReset (or any other teardown of the device's
+ * primary context), which would leave it stale.  All calls share the
+ * array: calls whose work overlaps on the GPU race, so order them on one
+ * stream.  Pointers must be aligned as for mppi_solve_async (MPPI_EINVAL
+ * otherwise).  Launch shape: 128 threads, one per sample. */
 int mppi_solve_noalloc(const mppi_model* model, const mppi_params* params, const float* x_hat,
                        const float* ref, const float* obstacles, int32_t M, const float* u_nom, uint64_t iter,
                        float* u_out, float* u_cmd, float* u_next, float* x_next, float* costs, int32_t* status,

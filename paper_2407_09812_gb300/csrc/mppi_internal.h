@@ -130,6 +130,7 @@ int check_step(int K, int N, float dt, float lambda, const float* sigma);
 DevModel make_dev_model(const mppi_model& m);
 DevCost make_dev_cost(const mppi_params& p);
 bool aligned16(const void* p);
+bool aligned4(const void* p);
 
 size_t smem_bytes(int N_max, int M_max, Shape s);
 bool shape_supported(Shape s);

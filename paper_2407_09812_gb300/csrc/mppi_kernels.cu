@@ -1261,24 +1261,33 @@ size_t smem_bytes(int N_max, int M_max, Shape s) {
     return smem_layout(N_max, M_max, s.block, s.lanes, s.pipe != 0).total;
 }
 
-// Largest dynamic shared memory opted in so far, per instantiation.  The
-// attribute is raised only when a launch needs more, so launches that are
-// being captured into a graph (after a first, uncaptured preparation) make
-// no attribute call.
+// Largest dynamic shared memory opted in so far, per instantiation and per
+// device (the attribute belongs to the device's context).  The attribute is
+// raised only when a launch needs more, so launches that are being captured
+// into a graph (after a first, uncaptured preparation) make no attribute
+// call.
+constexpr int kMaxDevices = 64;
+
 template <int LANES, bool PIPE, int MINB>
-static std::atomic<int>& smem_opt_in() {
-    static std::atomic<int> v{0};
-    return v;
+static std::atomic<int>* smem_opt_in() {
+    static std::atomic<int> v[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return nullptr;  // unknown device: set the attribute every time
+    }
+    return &v[dev];
 }
 
 template <int LANES, bool PIPE, int MINB>
 static cudaError_t prepare_t(size_t smem) {
-    if ((int)smem <= smem_opt_in<LANES, PIPE, MINB>().load()) return cudaSuccess;
+    std::atomic<int>* opt = smem_opt_in<LANES, PIPE, MINB>();
+    if (opt && (int)smem <= opt->load()) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(mppi_step_kernel<LANES, PIPE, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) {
-        int cur = smem_opt_in<LANES, PIPE, MINB>().load();
-        while ((int)smem > cur && !smem_opt_in<LANES, PIPE, MINB>().compare_exchange_weak(cur, (int)smem)) {
+    if (e == cudaSuccess && opt) {
+        int cur = opt->load();
+        while ((int)smem > cur && !opt->compare_exchange_weak(cur, (int)smem)) {
         }
     }
     return e;

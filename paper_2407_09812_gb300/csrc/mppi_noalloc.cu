@@ -16,7 +16,9 @@
 // name is only a host-side stand-in, so its device address is looked up
 // with cudaGetSymbolAddress, once per device, on the first call made with
 // that device current; that first call should therefore come before any
-// stream capture.  All calls share the array and it keeps the last call's
+// stream capture.  The looked-up address is kept for the life of the
+// process and is not valid after the device's primary context is torn
+// down (cudaDeviceReset).  All calls share the array and it keeps the last call's
 // contents: each call clears the counters that must start at zero, and
 // calls whose work overlaps on the GPU (different streams, no ordering)
 // race on the array.
@@ -78,7 +80,12 @@ extern "C" int mppi_solve_noalloc(const mppi_model* model, const mppi_params* pa
     if ((rc = check_params(params))) return rc;
     if (params->K > kNoAllocMaxK || params->N > kNoAllocMaxN) return MPPI_EINVAL;
     if (!x_hat || !ref || !u_nom || M < 0 || M > MPPI_M_MAX) return MPPI_EINVAL;
-    if (M > 0 && (!obstacles || (reinterpret_cast<uintptr_t>(obstacles) & 15u) != 0)) return MPPI_EINVAL;
+    if (M > 0 && (!obstacles || !aligned16(obstacles))) return MPPI_EINVAL;
+    // The kernel reads and writes these with 4-byte accesses: a misaligned
+    // pointer would fault on the device, so it is refused here.
+    const void* ptrs[] = {x_hat, ref, u_nom, u_out, u_cmd, u_next, x_next, costs, status};
+    for (const void* p : ptrs)
+        if (p && !aligned4(p)) return MPPI_EINVAL;
 
     const Shape shape{kNoAllocBlock, 1};
     const size_t smem = smem_bytes(params->N, M, shape);

@@ -173,3 +173,35 @@ def test_binding_address_cache_is_by_identity_and_bounded(built):
     assert len(c.d) <= 4
     assert all(e[0] is not a for e in c.d.values())  # evicted in insertion order
     assert c.get(a) == a.ctypes.data
+
+
+def test_noalloc_refuses_misaligned_and_oversized_arguments_on_the_host(built):
+    """mppi_solve_noalloc checks its arguments before it touches the device:
+    a state, reference, nominal or output pointer that is not 4-byte aligned
+    (the kernel's scalar accesses would fault), an obstacle pointer that is
+    not 16-byte aligned (it is staged by bulk copies), and sizes beyond its
+    fixed scratch (K > 32768 or N > 256) all return MPPI_EINVAL.  The
+    addresses are never dereferenced, so this runs without a GPU."""
+    from paper_2407_09812_gb300 import inputs as I
+    from paper_2407_09812_gb300 import mppi
+    L = mppi.lib()
+    m, p = mppi.make_model(I.model()), mppi.make_params(I.params(K=256, N=10))
+    base = 0x7f0000000000  # plausible, 256-byte aligned, never dereferenced
+    args = {"x_hat": base, "ref": base + 0x1000, "obstacles": base + 0x2000, "u_nom": base + 0x3000,
+            "u_out": base + 0x4000, "u_cmd": base + 0x5000, "u_next": base + 0x6000, "x_next": base + 0x7000,
+            "costs": base + 0x8000, "status": base + 0x9000}
+
+    def call(over=None, M=4, pp=p):
+        a = dict(args, **(over or {}))
+        return L.mppi_solve_noalloc(C.byref(m), C.byref(pp), a["x_hat"], a["ref"], a["obstacles"], M, a["u_nom"],
+                                    0, a["u_out"], a["u_cmd"], a["u_next"], a["x_next"], a["costs"], a["status"],
+                                    None)
+
+    for name in args:
+        off = 8 if name == "obstacles" else 2
+        assert call({name: args[name] + off}) == mppi.EINVAL, name
+    assert call({"x_hat": None}) == mppi.EINVAL
+    assert call({"obstacles": None}) == mppi.EINVAL
+    for K, N in ((32769, 10), (256, 257)):
+        pp = mppi.make_params(I.params(K=K, N=N))
+        assert call(pp=pp) == mppi.EINVAL, (K, N)

@@ -7,6 +7,8 @@ It is checked through the C ABI against the handle-based entry point
 calls in a row of different sizes (the second call reuses the fixed scratch
 array the first one left behind).  This file is collected last so that a
 run stopping at the first failure has already run every other test."""
+import os
+
 import numpy as np
 import pytest
 
@@ -60,20 +62,44 @@ def test_noalloc_matches_handle_entry_point_twice():
         assert cost_err(got["costs"], ref["costs"])[0] <= COST_RTOL
 
 
+def test_noalloc_at_its_scratch_limits_matches_the_oracle():
+    """K = 32768 and N = 256 fill the fixed scratch exactly (256 tiles of
+    128 samples, 4 + 4N floats each, after the 256-byte header).  The
+    result at those sizes is compared with the handle-based entry point and
+    with the FP64 oracle directly, within the parity tolerance."""
+    import torch
+    from oracle import oracle as O
+    from paper_2407_09812_gb300 import inputs as I
+    from paper_2407_09812_gb300 import mppi
+    prob = I.eight_with_spheres(K=32768, N=256, dt=0.004, M=12, t0=1.1, **{"lambda": 300.0})
+    got = _run(mppi, torch, prob, noalloc=True)
+    ref = _run(mppi, torch, prob, noalloc=False)
+    orc = O.mppi_step(prob, n_threads=os.cpu_count() or 1)
+    assert got["status"] == 0 and ref["status"] == 0
+    sig = prob["params"]["sigma"]
+    for want in (ref, orc):
+        assert control_err(got["u_out"], want["u_out"], sig) <= U_RTOL
+        assert control_err(got["u_next"], want["u_next"], sig) <= U_RTOL
+        assert control_err(got["u_cmd"], want["u_cmd"], sig) <= U_RTOL
+        assert cost_err(got["costs"], want["costs"], want.get("min_gap"))[0] <= COST_RTOL
+    assert state_err(got["x_next"], ref["x_next"]) <= U_RTOL
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     import torch
     from paper_2407_09812_gb300 import inputs as I
     from paper_2407_09812_gb300 import mppi
     x = torch.zeros(13, device="cuda")
-    big = I.plain_hover(K=40000, N=10)
+    big = I.plain_hover(K=32769, N=10)
     with pytest.raises(mppi.MppiError) as e:
         mppi.solve_noalloc(big["model"], big["params"], x, torch.zeros(11, 13, device="cuda"), None,
                            torch.zeros(10, 4, device="cuda"), 0)
     assert e.value.code == mppi.EINVAL
-    long = I.plain_hover(K=100, N=300)
-    with pytest.raises(mppi.MppiError):
-        mppi.solve_noalloc(long["model"], long["params"], x, torch.zeros(301, 13, device="cuda"), None,
-                           torch.zeros(300, 4, device="cuda"), 0)
+    long = I.plain_hover(K=100, N=257)
+    with pytest.raises(mppi.MppiError) as e:
+        mppi.solve_noalloc(long["model"], long["params"], x, torch.zeros(258, 13, device="cuda"), None,
+                           torch.zeros(257, 4, device="cuda"), 0)
+    assert e.value.code == mppi.EINVAL
     # Buffers that do not match K and N are refused before any call.
     ok = I.plain_hover(K=100, N=10)
     with pytest.raises(ValueError):
