@@ -1,25 +1,32 @@
-"""Benchmark of the MPPI step on GB300.
+"""Benchmark of the MPPI step on GB300: batched vs plain.
 
-Headline workload (one "step" = one control step of a closed loop): the
-figure-eight tracking problem with 64 spherical obstacles, K=16384 samples,
-N=100, dt=0.01 s, per-motor thrust limits.  Each step solves one MPPI
-iteration on device-resident inputs (state, reference window, obstacles,
-warm-start nominal), then the simulated vehicle advances by the applied
-command (the kernel's x_next) and the warm start is the shifted nominal.
+Headline workload (one "step" = one control step of a fleet): 256
+independent vehicles with uneven problem sizes (K log-uniform in [1024,
+32768], N uniform in [30, 150], dt = 0.01 s, 0-128 spheres each, own seeded
+initial state and figure-eight phase) solved in ONE persistent launch of the
+fused MPPI kernel replayed from a CUDA graph, with the launch shape picked by
+the project's batch autotuner.  The fleet runs closed loop on device-resident
+inputs: every step each vehicle's warm start is the previous step's shifted
+nominal, its state the previous step's plant state, its reference window
+advances by dt and its Philox counter by one.
 
-Printed: one JSON line with rollout-steps/s (K*N per second), solves/s,
-p50/p99 latency, an end-to-end figure through the host-buffer C ABI, the
-roofline of the fused kernel, the CPU oracle timed on the host cores, the
-batched (256 uneven instances, persistent kernel, CUDA graph) and served
-(continuous batching) forms, and the SM clocks seen during the timed region.
+Printed: one JSON line with rollout-steps/s (sum of K*N per second), solves/s
+and p50/p99 launch latency; an end-to-end figure through the host-buffer
+batched C ABI (mppi_solve_batch_host); the roofline of the batched kernel
+against FP32 FMA and MUFU rates measured in the same run; the CPU oracle
+timed on the host cores on the same instances; and, as sub-keys, the plain
+single-instance paths (the plain step, the same 256 vehicles one launch
+each), the single-vehicle closed loop with obstacles, the large-scale stress
+solve with its FP64-oracle error, the paper's operating point, the method's
+options, the serving loop, and the SM clocks seen while the GPU worked.
 
-`--impl reference` times the FP64 CPU oracle on the same workload instead.
+`--impl reference` times the FP64 CPU oracle on the same instances instead.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -33,66 +40,96 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MPPI rollout-steps/s, solves/s, p50/p99 solve latency: batched vs plain, 1 GB300"
 UNIT = "rollout-steps/s"
+N_FLEET, FLEET_SEED, FLEET_DT = 256, 2, 0.01
+WORKLOAD = ("batched uneven fleet: 256 vehicles, K log-uniform [1024, 32768], N uniform [30, 150], "
+            "dt=0.01 s, 0-128 spheres each, own initial state and figure-eight phase; one persistent "
+            "launch per control step under CUDA-graph replay, closed loop")
 K_HEAD, N_HEAD, DT_HEAD, M_HEAD = 16384, 100, 0.01, 64
-WORKLOAD = ("closed-loop figure-eight tracking, K=16384, N=100, dt=0.01 s, 64 spheres, "
-            "per-motor thrust limits, lambda=1")
+CLOSED_LOOP = ("closed-loop figure-eight tracking, K=16384, N=100, dt=0.01 s, 64 spheres, "
+               "per-motor thrust limits, lambda=1")
 
-# Algorithmic FP32 work per rollout-step and per evaluated (state,
-# obstacle) pair, counted from the equations of the method as the oracle
-# writes them: per rollout step noise 24, perturb + clamp 12, input and rate
-# cost 27, constraint pipeline 95, RK4 437, renormalisation 12, tracking
-# cost 43; per pair 17.  Pairs whose barrier term is below its floor (2^-48
-# of c_bar, where it counts as zero) and that cannot be in collision are not
-# part of the result and are not counted; the kernel reports how many pairs
-# it evaluated (mppi_set_counters).
+# Algorithmic work, counted from the equations of the method as the oracle
+# writes them.  FP32 per rollout step: noise 24, perturb + clamp 12, input
+# and rate cost 27, constraint pipeline 95, RK4 437, renormalisation 12,
+# tracking cost 43; per evaluated (state, obstacle) pair 17.  MUFU per
+# rollout step: Box-Muller 2 lg2, 2 square roots (as rsqrt), 2 sin, 2 cos;
+# renormalisation 1 rsqrt; per evaluated pair 1 ex2.  Pairs whose barrier
+# term is below its floor (2^-48 of c_bar, where it counts as zero) and that
+# cannot be in collision are not part of the result and are not counted;
+# the kernel reports how many pairs it evaluated (mppi_set_counters).
 FLOP_PER_STEP = 650
 FLOP_PER_PAIR = 17
+MUFU_PER_STEP = {"lg2_ops": 2, "rsqrt_ops": 3, "sin_ops": 2, "cos_ops": 2}
+MUFU_PER_PAIR = {"ex2_ops": 1}
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the headline kernel in an ncu capture of this workload: the inputs, the
-# partials and the outputs; everything else stays on chip.  Taken for the
-# kernel as it is; set to None when the kernel changes until recaptured.
-HEADLINE_TRAFFIC_BYTES = 122624
-SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+# the kernel in an ncu capture of the named workload, valid only for the
+# kernel source it was taken with (sha256 of the kernel file and its header,
+# first 16 hex digits); any other source reports null.
+TRAFFIC_CAPTURES = {}
+KERNEL_FILES = ("paper_2407_09812_gb300/csrc/mppi_kernels.cu", "paper_2407_09812_gb300/csrc/mppi_internal.h")
 
 
-def fp32_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
-    return SMS * LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_FILES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(workload: str):
+    c = TRAFFIC_CAPTURES.get(workload)
+    if c and c["kernel_sha"] == kernel_sha():
+        return c["bytes"]
+    return None
 
 
 # ---------------------------------------------------------------- helpers
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi SM clocks and throttle reasons, sampled every 100 ms from
+    before the first GPU section to the end of the last one; each sample
+    carries the host time it arrived, so a section's share can be picked."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.samples = []  # (host time, sm MHz, max MHz, power W, reasons)
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
             t0 = time.time()
-            while not self.lines and time.time() - t0 < 5.0:  # first sample before timing starts
-                time.sleep(0.005)
-            self.lines.clear()
+            while not self.samples and time.time() - t0 < 5.0:
+                time.sleep(0.01)
         except (OSError, ValueError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            p = [x.strip() for x in line.strip().split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm, mx = float(p[1]), float(p[2])
+                pw = float(p[3]) if p[3].replace(".", "", 1).isdigit() else float("nan")
+            except ValueError:
+                continue
+            reasons = {n for n, v in zip(self.NAMES, p[5:9]) if v.lower() == "active"}
+            self.samples.append((time.perf_counter(), sm, mx, pw, reasons))
 
-    def __exit__(self, *a):
+    def stop(self):
         if self.proc:
             self.proc.terminate()
             try:
@@ -100,28 +137,17 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self) -> dict:
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            p = [x.strip() for x in ln.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                sm.append(float(p[1]))
-                mx.append(float(p[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, p[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+    def summary(self, t0=None, t1=None) -> dict:
+        sel = [s for s in self.samples if (t0 is None or s[0] >= t0) and (t1 is None or s[0] <= t1)]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        reasons = set().union(*[s[4] for s in sel])
+        return {"sm_mhz": float(np.median([s[1] for s in sel])), "sm_max_mhz": float(max(s[2] for s in sel)),
+                "reasons": sorted(reasons), "samples": len(sel),
+                "power_w_max": float(np.nanmax([s[3] for s in sel]))}
 
 
-def dist_setup(n_gpus: int):
+def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -151,16 +177,310 @@ def barrier(world: int):
 
 def whole_job_rate(units_per_step_per_rank: float, steps: int, max_ms: float, world: int) -> float:
     """Units processed by all ranks divided by the slowest rank's time
-    (replicas: every rank solves its own vehicle; weak scaling)."""
+    (replicas: every rank solves its own fleet; weak scaling)."""
     return world * units_per_step_per_rank * steps / (max_ms * 1e-3)
 
 
-# --------------------------------------------------------------- workload
+def roofline(flop: float, mufu: dict, ms: float, peaks: dict, traffic, what: str) -> dict:
+    """FP32 and MUFU fractions of one launch of `ms` milliseconds against
+    the rates measured in this run."""
+    achieved = flop / (ms * 1e-3) / 1e12
+    peak = peaks["fp32_flops"] / 1e12
+    mufu_s = sum(n / peaks[op] for op, n in mufu.items())
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu capture of this kernel source)",
+            "kernel": f"mppi_step_kernel ({what})",
+            "peak_source": "of measured: FFMA micro-benchmark (mppi_measure_peaks) in this run",
+            "mufu": {"ops_per_launch": float(sum(mufu.values())), "frac": mufu_s / (ms * 1e-3),
+                     "note": "time the launch's MUFU work needs at the measured MUFU rates / launch time"}}
 
-def headline_problem(rank: int):
+
+def mufu_ops(rollout_steps: float, pairs: float) -> dict:
+    out = {op: rollout_steps * n for op, n in MUFU_PER_STEP.items()}
+    for op, n in MUFU_PER_PAIR.items():
+        out[op] = out.get(op, 0.0) + pairs * n
+    return out
+
+
+def shape_dict(s) -> dict:
+    return {"block": s[0], "lanes": s[1], "pipelined": s[2], "list_margin": s[3]}
+
+
+def flusher():
+    import torch
+    return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+
+
+# ------------------------------------------------------------- the fleet
+
+class Fleet:
+    """The headline workload's 256 vehicles laid out for the batched entry
+    points: every per-vehicle array is a slice of one flat array (device or
+    host), so a step's descriptors are updated with vectorised operations.
+    The reference of vehicle i is one long sampled trajectory; the window
+    of step t starts 13 t floats in."""
+
+    def __init__(self, n_steps: int, stream_base: int = 0):
+        from paper_2407_09812_gb300 import inputs as I
+        self.probs = I.batched_uneven(n=N_FLEET, seed=FLEET_SEED, dt=FLEET_DT)
+        for i, p in enumerate(self.probs):
+            p["params"] = dict(p["params"], stream_id=stream_base + i)
+        self.n = len(self.probs)
+        self.K = np.array([p["params"]["K"] for p in self.probs], np.int64)
+        self.N = np.array([p["params"]["N"] for p in self.probs], np.int64)
+        self.M = np.array([p["obstacles"].shape[0] for p in self.probs], np.int64)
+        self.rollout_steps = int((self.K * self.N).sum())
+        self.n_steps = n_steps
+        # Flat layouts (float offsets; every segment a multiple of 4 floats).
+        self.rlen = 13 * (n_steps + self.N + 1)
+        self.roff = np.concatenate([[0], np.cumsum((self.rlen + 3) // 4 * 4)[:-1]])
+        self.uoff = np.concatenate([[0], np.cumsum(4 * self.N)[:-1]])
+        self.ooff = np.concatenate([[0], np.cumsum(4 * self.M)[:-1]])
+        ref = np.zeros(int(((self.rlen + 3) // 4 * 4).sum()), np.float32)
+        for i, p in enumerate(self.probs):
+            traj = I.Trajectory("eight", {"phase": p["phase"]})
+            w = traj.window(0.0, int(n_steps + self.N[i]), FLEET_DT)
+            ref[self.roff[i]:self.roff[i] + w.size] = w.reshape(-1)
+        self.ref = ref
+        self.obs = np.concatenate([p["obstacles"].reshape(-1) for p in self.probs]).astype(np.float32)
+        self.x0 = np.zeros((self.n, 16), np.float32)
+        self.u0 = np.concatenate([p["u_nom"].reshape(-1) for p in self.probs]).astype(np.float32)
+        for i, p in enumerate(self.probs):
+            self.x0[i, :13] = p["x_hat"]
+        self.iter0 = np.array([p["iter"] for p in self.probs], np.uint64)
+
+    def records(self, INSTANCE_DTYPE, base: dict, ping: int) -> np.ndarray:
+        """Descriptors of one ping-pong phase: state and nominal read from
+        buffer `ping`, warm start and plant state written to the other.
+        `base` holds the flat arrays' addresses."""
+        r = np.zeros(self.n, INSTANCE_DTYPE)
+        a, b = ping, 1 - ping
+        r["x_hat"] = base["x"][a] + 64 * np.arange(self.n)
+        r["x_next"] = base["x"][b] + 64 * np.arange(self.n)
+        r["u_nom"] = base["u"][a] + 4 * self.uoff
+        r["u_next"] = base["u"][b] + 4 * self.uoff
+        r["u_out"] = base["u_out"] + 4 * self.uoff
+        r["u_cmd"] = base["u_cmd"] + 16 * np.arange(self.n)
+        r["status"] = base["status"] + 4 * np.arange(self.n)
+        r["obstacles"] = np.where(self.M > 0, base["obs"] + 4 * self.ooff, 0)
+        r["ref"] = base["ref"] + 4 * self.roff
+        r["iter"] = self.iter0
+        r["K"], r["N"], r["M"] = self.K, self.N, self.M
+        for i, p in enumerate(self.probs):
+            q = p["params"]
+            r["dt"][i], r["lam"][i], r["sigma"][i] = q["dt"], q["lambda"], q["sigma"]
+            r["seed"][i], r["stream_id"][i] = q["seed"], q["stream_id"]
+        return r
+
+    def device_buffers(self):
+        import torch
+        dev = torch.device("cuda")
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        b = {"x": [t(self.x0), t(self.x0)], "u": [t(self.u0), t(self.u0)], "ref": t(self.ref),
+             "obs": t(self.obs) if self.obs.size else torch.zeros(4, device=dev),
+             "u_out": torch.zeros(self.u0.size, device=dev), "u_cmd": torch.zeros(self.n, 4, device=dev),
+             "status": torch.zeros(self.n, dtype=torch.int32, device=dev)}
+        addr = {k: ([v[0].data_ptr(), v[1].data_ptr()] if isinstance(v, list) else v.data_ptr())
+                for k, v in b.items()}
+        return b, addr
+
+    def host_buffers(self):
+        import torch
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        b = {"x": [pin(self.x0), pin(self.x0)], "u": [pin(self.u0), pin(self.u0)], "ref": pin(self.ref),
+             "obs": pin(self.obs if self.obs.size else np.zeros(4, np.float32)),
+             "u_out": pin(np.zeros(self.u0.size, np.float32)), "u_cmd": pin(np.zeros((self.n, 4), np.float32)),
+             "status": pin(np.zeros(self.n, np.int32))}
+        addr = {k: ([v[0].ctypes.data, v[1].ctypes.data] if isinstance(v, list) else v.ctypes.data)
+                for k, v in b.items()}
+        return b, addr
+
+    def dicts(self, bufs, ping=0):
+        """The fleet as per-instance dicts of torch tensors (for the tuner and
+        the one-by-one launches), sharing the flat device buffers."""
+        out = []
+        a = ping
+        for i, p in enumerate(self.probs):
+            N, M, u0 = int(self.N[i]), int(self.M[i]), int(self.uoff[i])
+            q = p["params"]
+            out.append({"x_hat": bufs["x"][a][i, :13], "ref": bufs["ref"][self.roff[i]:self.roff[i] + 13 * (N + 1)],
+                        "obstacles": bufs["obs"][self.ooff[i]:self.ooff[i] + 4 * M] if M else None,
+                        "u_nom": bufs["u"][a][u0:u0 + 4 * N], "u_out": bufs["u_out"][u0:u0 + 4 * N],
+                        "u_cmd": bufs["u_cmd"][i], "K": int(self.K[i]), "N": N, "dt": q["dt"],
+                        "lambda": q["lambda"], "sigma": q["sigma"], "seed": q["seed"], "stream_id": q["stream_id"],
+                        "iter": int(self.iter0[i])})
+        return out
+
+    def h2d_d2h_bytes(self):
+        """Bytes of mppi_solve_batch_host's two copies (16-byte segments)."""
+        up4 = lambda v: (v + 3) // 4 * 4
+        h2d = 4 * int((16 + up4(13 * (self.N + 1)) + 4 * self.M + 4 * self.N).sum())
+        d2h = 4 * int((8 * self.N + 24).sum())
+        return h2d, d2h
+
+
+def run_fleet(args, rank: int, peaks: dict, clk: ClockSampler):
+    """The headline: batch-autotuned shape, then W untimed and K timed
+    closed-loop steps, one graph-replayed persistent launch each, timed
+    with CUDA events on the launching stream; the L2 is flushed between
+    steps outside the events."""
+    import torch
+    from paper_2407_09812_gb300 import mppi
+    n_total = args.warmup + args.steps
+    fleet = Fleet(n_total, stream_base=rank * N_FLEET)
+    bufs, addr = fleet.device_buffers()
+    rec = [fleet.records(mppi.INSTANCE_DTYPE, addr, 0), fleet.records(mppi.INSTANCE_DTYPE, addr, 1)]
+    cap = {"max_instances": fleet.n, "max_samples": int(fleet.K.sum()), "N_max": int(fleet.N.max()),
+           "M_max": int(max(1, fleet.M.max()))}
+    p0 = fleet.probs[0]
+    solver = mppi.Solver(p0["model"], p0["params"], cap)
+    stream = torch.cuda.current_stream()
+    t_tune = time.perf_counter()
+    shape = solver.autotune_batch(fleet.dicts(bufs), stream=stream)
+    t_tune = time.perf_counter() - t_tune
+    pairs = torch.zeros(1, dtype=torch.int64, device="cuda")
+    solver.set_counters(pairs)  # evaluated obstacle pairs of step 0, in an untimed launch
+    solver.solve_batch(rec[0], stream=stream, graph=False)
+    torch.cuda.synchronize()
+    pairs_per_launch = int(pairs.item())
+    solver.set_counters(None)
+    flush = flusher()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_total)]
+
+    def step(i):
+        r = rec[i % 2]
+        r["ref"] = addr["ref"] + 4 * fleet.roff + 52 * i
+        r["iter"] = fleet.iter0 + np.uint64(i)
+        solver.solve_batch(r, stream=stream, graph=True)
+
+    for i in range(args.warmup):
+        flush.zero_()
+        step(i)
+    torch.cuda.synchronize()
+    barrier(args.world)
+    t0 = time.perf_counter()
+    for i in range(args.warmup, n_total):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step(i)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    barrier(args.world)
+    ms = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(args.warmup, n_total)])
+    status = bufs["status"].cpu().numpy()
+    final_x = bufs["x"][n_total % 2].cpu().numpy()
+    solver.close()
+    return {"ms": ms, "fleet": fleet, "shape": shape, "tune_s": t_tune, "pairs": pairs_per_launch,
+            "status_ok": int((status == 0).sum()), "finite": bool(np.all(np.isfinite(final_x))),
+            "window": (t0, t1)}
+
+
+def run_fleet_e2e(args, fleet: Fleet, shape, n_steps: int):
+    """The same closed loop through mppi_solve_batch_host with HOST buffers
+    (pinned): every step packs the fleet's inputs, copies them in, solves,
+    copies the outputs back and unpacks them."""
+    from paper_2407_09812_gb300 import mppi
+    bufs, addr = fleet.host_buffers()
+    rec = [fleet.records(mppi.INSTANCE_DTYPE, addr, 0), fleet.records(mppi.INSTANCE_DTYPE, addr, 1)]
+    p0 = fleet.probs[0]
+    cap = {"max_instances": fleet.n, "max_samples": int(fleet.K.sum()), "N_max": int(fleet.N.max()),
+           "M_max": int(max(1, fleet.M.max()))}
+    solver = mppi.Solver(p0["model"], p0["params"], cap)
+    solver.set_shape(*shape)
+    lat = []
+    for i in range(n_steps + 3):
+        r = rec[i % 2]
+        r["ref"] = addr["ref"] + 4 * fleet.roff + 52 * i
+        r["iter"] = fleet.iter0 + np.uint64(i)
+        t0 = time.perf_counter()
+        solver.solve_batch_host(r)
+        dt = time.perf_counter() - t0
+        if i >= 3:
+            lat.append(dt)
+    solver.close()
+    lat = np.array(lat)
+    h2d, d2h = fleet.h2d_d2h_bytes()
+    return {"value": fleet.rollout_steps / float(lat.mean()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": float(lat.mean() * 1e3),
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "solves_per_s": fleet.n / float(lat.mean()),
+            "api": "mppi_solve_batch_host (host buffers, one packed copy each way, synchronous)"}
+
+
+def run_one_by_one(fleet: Fleet):
+    """The same 256 instances, one single-instance launch each (the plain
+    path), device buffers, each launch with the handle's default shape."""
+    import torch
+    from paper_2407_09812_gb300 import mppi
+    bufs, _ = fleet.device_buffers()
+    insts = fleet.dicts(bufs)
+    plain = mppi.Solver(fleet.probs[0]["model"], fleet.probs[0]["params"],
+                        {"max_instances": 1, "max_samples": 32768, "N_max": 150, "M_max": 128})
+    stream = torch.cuda.current_stream()
+    flush = flusher()
+
+    def one_pass():
+        for p, d in zip(fleet.probs, insts):
+            plain.set_params(p["params"])
+            plain.solve_async(d["x_hat"], d["ref"], d["obstacles"], d["u_nom"], d["iter"], u_out=d["u_out"],
+                              u_cmd=d["u_cmd"], stream=stream)
+
+    one_pass()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(3):
+        flush.zero_()
+        e0.record(stream)
+        one_pass()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    plain.close()
+    ms = float(np.median(times))
+    return {"workload": "the same 256 instances, one single-instance launch each (default shapes)",
+            "ms_total": ms, "rollout_steps_per_s": fleet.rollout_steps / (ms * 1e-3),
+            "solves_per_s": fleet.n / (ms * 1e-3)}
+
+
+def run_plain_step(reps=30):
+    """The plain single MPPI step: K=1024, N=50, dt=0.02, hover reference,
+    0.5 m offset, box-clamped inputs, no obstacles; device buffers, L2
+    flushed before each solve, CUDA events per solve."""
+    import torch
     from paper_2407_09812_gb300 import inputs as I
-    prob = I.eight_with_spheres(K=K_HEAD, N=N_HEAD, dt=DT_HEAD, M=M_HEAD, seed=1, stream_id=rank)
-    return prob
+    from paper_2407_09812_gb300 import mppi
+    prob = I.plain_hover()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, r, u = t(prob["x_hat"]), t(prob["ref"]), t(prob["u_nom"])
+    uo = torch.zeros(50, 4, device="cuda")
+    s = mppi.Solver(prob["model"], prob["params"])
+    flush = flusher()
+    ts = []
+    for i in range(reps + 3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.solve_async(x, r, None, u, i, u_out=uo)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 3:
+            ts.append(e0.elapsed_time(e1))
+    shape = s.get_shape(1024, 50, 0)
+    s.close()
+    ts = np.array(ts)
+    return {"workload": "plain step: K=1024, N=50, dt=0.02 s, hover reference, 0.5 m offset, box clamp, no obstacles",
+            "ms_per_solve": float(np.median(ts)), "p99_ms": float(np.percentile(ts, 99)),
+            "rollout_steps_per_s": 1024 * 50 / (float(np.median(ts)) * 1e-3),
+            "solves_per_s": 1e3 / float(np.median(ts)), "shape": shape_dict(shape)}
+
+
+# -------------------------------------------- single-vehicle closed loop
+
+def headline_problem(rank: int = 0):
+    from paper_2407_09812_gb300 import inputs as I
+    return I.eight_with_spheres(K=K_HEAD, N=N_HEAD, dt=DT_HEAD, M=M_HEAD, seed=1, stream_id=rank)
 
 
 def reference_windows(n_steps: int):
@@ -169,14 +489,17 @@ def reference_windows(n_steps: int):
     return np.stack([traj.window(DT_HEAD * t, N_HEAD, DT_HEAD) for t in range(n_steps)])
 
 
-def run_closed_loop(args, rank):
+def run_closed_loop(n_steps: int, peaks: dict, warmup=5):
+    """One vehicle, K=16384, N=100, 64 spheres: closed loop on device
+    buffers, one solve per control step (CUDA events per solve, L2 flushed
+    between), then the same loop through mppi_solve with host buffers."""
     import torch
     from paper_2407_09812_gb300 import mppi
-
     dev = torch.device("cuda")
-    prob = headline_problem(rank)
-    n_total = args.warmup + args.steps
-    refs = torch.from_numpy(reference_windows(n_total)).to(dev)
+    prob = headline_problem()
+    n_total = warmup + n_steps
+    refs_h = reference_windows(n_total)
+    refs = torch.from_numpy(refs_h).to(dev)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     obs = t(prob["obstacles"])
     x = [t(prob["x_hat"]), torch.zeros(13, device=dev)]
@@ -185,7 +508,10 @@ def run_closed_loop(args, rank):
     u_cmd = torch.zeros(4, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     solver = mppi.Solver(prob["model"], prob["params"])
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    shape = solver.autotune_on({"x_hat": x[0], "ref": refs[0], "obstacles": obs, "u_nom": u[0], "K": K_HEAD,
+                                "N": N_HEAD, "dt": DT_HEAD, "lambda": prob["params"]["lambda"],
+                                "sigma": prob["params"]["sigma"], "seed": prob["params"]["seed"], "iter": 0})
+    flush = flusher()
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_total)]
 
@@ -195,140 +521,63 @@ def run_closed_loop(args, rank):
                            status=status, stream=stream)
 
     pairs = torch.zeros(1, dtype=torch.int64, device=dev)
-    solver.set_counters(pairs)  # evaluated obstacle pairs, counted in the warm-up only
-    for i in range(args.warmup):
+    solver.set_counters(pairs)
+    for i in range(warmup):
         flush.zero_()
         step(i)
     torch.cuda.synchronize()
-    pairs_per_solve = int(pairs.item()) / args.warmup
+    pairs_per_solve = int(pairs.item()) / warmup
     solver.set_counters(None)
-    barrier(args.world)
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        wall0 = time.perf_counter()
-        for i in range(args.warmup, n_total):
-            flush.zero_()  # L2 flush between timed steps, outside the events
-            ev[i][0].record(stream)
-            step(i)
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-    barrier(args.world)
-    ms = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(args.warmup, n_total)])
+    for i in range(warmup, n_total):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step(i)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(warmup, n_total)])
     st = int(status.item())
-    final_x = x[n_total % 2].cpu().numpy()
     solver.close()
-    return {"ms": ms, "wall": wall, "clocks": clk.summary(), "status": st, "final_x": final_x,
-            "x_trace_ok": bool(np.all(np.isfinite(final_x))), "pairs_per_solve": pairs_per_solve}
-
-
-def run_e2e(args, rank, n_steps):
-    """Same closed loop through mppi_solve with HOST buffers: every step
-    copies its inputs host->device and its results device->host."""
-    from paper_2407_09812_gb300 import mppi
-    prob = headline_problem(rank)
-    refs = reference_windows(n_steps + 3)
+    # Host buffers through mppi_solve.
     solver = mppi.Solver(prob["model"], prob["params"])
-    x, u = prob["x_hat"].copy(), prob["u_nom"].copy()
+    solver.set_shape(*shape)
+    xh, uh = prob["x_hat"].copy(), prob["u_nom"].copy()
     lat = []
-    for i in range(n_steps + 3):
+    n_e2e = min(n_steps, 100)
+    for i in range(n_e2e + 3):
         t0 = time.perf_counter()
-        out = solver.solve(x, refs[i], prob["obstacles"], u, i)
+        out = solver.solve(xh, refs_h[i % n_total], prob["obstacles"], uh, i)
         dt = time.perf_counter() - t0
-        x, u = out["x_next"], out["u_next"]
+        xh, uh = out["x_next"], out["u_next"]
         if i >= 3:
             lat.append(dt)
     solver.close()
-    # Bytes of the two copies mppi_solve makes (16-byte aligned segments):
-    # in: x_hat and the Philox counter, reference, obstacles, nominal; out:
-    # u_out, u_cmd, u_next, x_next, status.
+    lat = np.array(lat)
     N, M = N_HEAD, M_HEAD
     up4 = lambda v: (v + 3) // 4 * 4
     h2d = 4 * up4(up4(up4(16 + 13 * (N + 1)) + 4 * M) + 4 * N)
     d2h = 4 * (up4(4 * N) + 4 + up4(4 * N) + 16 + 4)
-    lat = np.array(lat)
-    return {"value": K_HEAD * N_HEAD / float(lat.mean()), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": float(lat.mean() * 1e3),
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "api": "mppi_solve (host buffers, synchronous)"}
+    steps = K_HEAD * N_HEAD
+    mean = float(ms.mean())
+    return {"workload": CLOSED_LOOP, "steps": n_steps, "shape": shape_dict(shape),
+            "ms_per_solve": mean, "rollout_steps_per_s": steps / (mean * 1e-3), "solves_per_s": 1e3 / mean,
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "status_last_step": st,
+            "roofline": roofline(steps * FLOP_PER_STEP + pairs_per_solve * FLOP_PER_PAIR,
+                                 mufu_ops(steps, pairs_per_solve), mean, peaks, captured_traffic("closed_loop"),
+                                 "single instance"),
+            "obstacle_pairs": {"evaluated": pairs_per_solve, "all": K_HEAD * (N_HEAD + 1) * M_HEAD},
+            "e2e": {"value": steps / float(lat.mean()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": float(lat.mean() * 1e3),
+                    "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                    "api": "mppi_solve (host buffers, synchronous)"}}
 
 
-def run_batched(args, reps=5):
-    """256 uneven instances (K log-uniform 1024..32768, N 30..150, 0..128
-    spheres) in one persistent launch replayed from a CUDA graph, against
-    solving the same instances one launch each."""
-    import torch
-    from paper_2407_09812_gb300 import inputs as I
-    from paper_2407_09812_gb300 import mppi
-    dev = torch.device("cuda")
-    probs = I.batched_uneven(n=256, seed=2)
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    insts = []
-    for p in probs:
-        N = p["params"]["N"]
-        insts.append({"x_hat": t(p["x_hat"]), "ref": t(p["ref"]), "u_nom": t(p["u_nom"]),
-                      "obstacles": t(p["obstacles"]) if p["obstacles"].size else None,
-                      "u_out": torch.zeros(N, 4, device=dev), "u_cmd": torch.zeros(4, device=dev),
-                      "K": p["params"]["K"], "N": N, "dt": p["params"]["dt"], "lambda": p["params"]["lambda"],
-                      "sigma": p["params"]["sigma"], "seed": p["params"]["seed"],
-                      "stream_id": p["params"]["stream_id"], "iter": p["iter"]})
-    sumK = sum(i["K"] for i in insts)
-    steps = sum(i["K"] * i["N"] for i in insts)
-    cap = {"max_instances": len(insts), "max_samples": sumK, "N_max": 150, "M_max": 128}
-    m = probs[0]["model"]
-    solver = mppi.Solver(m, probs[0]["params"], cap)
-    stream = torch.cuda.current_stream()
-    pairs = torch.zeros(1, dtype=torch.int64, device=dev)
-    solver.set_counters(pairs)
-    solver.solve_batch(insts, stream=stream, graph=False)
-    torch.cuda.synchronize()
-    pairs_per_launch = int(pairs.item())
-    solver.set_counters(None)
-    for _ in range(2):
-        solver.solve_batch(insts, stream=stream, graph=True)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        solver.solve_batch(insts, stream=stream, graph=True)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1) / reps
-    # Plain: the same instances, one single-instance launch each.
-    plain = mppi.Solver(m, probs[0]["params"], {"max_instances": 1, "max_samples": 32768, "N_max": 150,
-                                                "M_max": 128})
+# ----------------------------------------------------------------- stress
 
-    def plain_pass():
-        for p, i in zip(probs, insts):
-            plain.set_params(p["params"])
-            plain.solve_async(i["x_hat"], i["ref"], i["obstacles"], i["u_nom"], i["iter"], u_out=i["u_out"],
-                              u_cmd=i["u_cmd"], stream=stream)
-
-    plain_pass()
-    torch.cuda.synchronize()
-    e0.record()
-    plain_pass()
-    e1.record()
-    torch.cuda.synchronize()
-    ms_p = e0.elapsed_time(e1)
-    plain.close()
-    solver.close()
-    all_pairs = sum(i["K"] * (i["N"] + 1) * (0 if i["obstacles"] is None else i["obstacles"].shape[0])
-                    for i in insts)
-    flop = steps * FLOP_PER_STEP + pairs_per_launch * FLOP_PER_PAIR
-    return {"workload": "256 uneven instances, K log-uniform [1024, 32768], N U[30,150], dt=0.01, 0-128 spheres",
-            "instances": len(insts), "rollout_steps_per_launch": steps,
-            "obstacle_pairs": {"evaluated": pairs_per_launch, "all": all_pairs},
-            "method_tflops": flop / (ms_b * 1e-3) / 1e12,
-            "frac_of_fp32_peak": flop / (ms_b * 1e-3) / 1e12 / fp32_peak_tflops(),
-            "batched_graph": {"ms_per_launch": ms_b, "rollout_steps_per_s": steps / (ms_b * 1e-3),
-                              "solves_per_s": len(insts) / (ms_b * 1e-3)},
-            "plain_sequential": {"ms_total": ms_p, "rollout_steps_per_s": steps / (ms_p * 1e-3),
-                                 "solves_per_s": len(insts) / (ms_p * 1e-3)}}
-
-
-def run_stress(reps=3):
+def run_stress(peaks: dict, reps=3):
     """K=262144, N=200, dt=0.005, 512 spheres + 512 pillars: one solve per
-    repetition on device buffers."""
+    repetition on device buffers with the instance-autotuned shape; the
+    outputs of the last solve are kept for the oracle comparison."""
     import torch
     from paper_2407_09812_gb300 import inputs as I
     from paper_2407_09812_gb300 import mppi
@@ -337,28 +586,71 @@ def run_stress(reps=3):
     K, N, M = prob["params"]["K"], prob["params"]["N"], prob["obstacles"].shape[0]
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     x, r, o, u = t(prob["x_hat"]), t(prob["ref"]), t(prob["obstacles"]), t(prob["u_nom"])
-    u_out = torch.zeros(N, 4, device=dev)
+    out = {k: torch.zeros(n, device=dev) for k, n in (("u_out", (N, 4)), ("u_cmd", 4), ("u_next", (N, 4)),
+                                                       ("x_next", 13), ("costs", K))}
     s = mppi.Solver(prob["model"], prob["params"])
+    shape = s.autotune_on({"x_hat": x, "ref": r, "obstacles": o, "u_nom": u, "K": K, "N": N,
+                           "dt": prob["params"]["dt"], "lambda": prob["params"]["lambda"],
+                           "sigma": prob["params"]["sigma"], "seed": prob["params"]["seed"], "iter": 0})
     pairs = torch.zeros(1, dtype=torch.int64, device=dev)
     s.set_counters(pairs)
-    s.solve_async(x, r, o, u, 0, u_out=u_out)
+    s.solve_async(x, r, o, u, prob["iter"], u_out=out["u_out"])
     torch.cuda.synchronize()
     n_pairs = int(pairs.item())
     s.set_counters(None)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    flush = flusher()
+    ts = []
     for i in range(reps):
-        s.solve_async(x, r, o, u, i, u_out=u_out)
-    e1.record()
-    torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.solve_async(x, r, o, u, prob["iter"], **out)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
     s.close()
-    ms = e0.elapsed_time(e1) / reps
-    flop = K * N * FLOP_PER_STEP + n_pairs * FLOP_PER_PAIR
-    return {"workload": "K=262144, N=200, dt=0.005, 512 spheres + 512 vertical cylinders, 12 m/s line",
-            "ms_per_solve": ms, "rollout_steps_per_s": K * N / (ms * 1e-3),
-            "obstacle_pairs": {"evaluated": n_pairs, "all": K * (N + 1) * M},
-            "method_tflops": flop / (ms * 1e-3) / 1e12, "frac_of_fp32_peak": flop / (ms * 1e-3) / 1e12 / fp32_peak_tflops()}
+    ms = float(np.median(ts))
+    steps = K * N
+    res = {"workload": "K=262144, N=200, dt=0.005, 512 spheres + 512 vertical cylinders, 12 m/s line",
+           "shape": shape_dict(shape), "ms_per_solve": ms, "rollout_steps_per_s": steps / (ms * 1e-3),
+           "obstacle_pairs": {"evaluated": n_pairs, "all": K * (N + 1) * M},
+           "roofline": roofline(steps * FLOP_PER_STEP + n_pairs * FLOP_PER_PAIR, mufu_ops(steps, n_pairs), ms,
+                                peaks, captured_traffic("stress"), "single instance")}
+    gpu = {k: v.cpu().numpy() for k, v in out.items()}
+    return res, prob, gpu
 
+
+def stress_oracle_error(prob, gpu) -> tuple:
+    """The FP64 oracle's full step on the stress problem (all host cores),
+    outside every timed region: relative errors of the GPU's update, warm
+    start, command and per-sample costs (the update error per control is
+    measured against max(|u_oracle|, sigma_c)); the oracle's time is that
+    workload's CPU baseline."""
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref = O.mppi_step(prob, n_threads=threads)
+    el = time.perf_counter() - t0
+    sig = np.asarray(prob["params"]["sigma"], np.float64)
+
+    def uerr(a, b):
+        a, b = np.asarray(a, np.float64).reshape(-1, 4), np.asarray(b, np.float64).reshape(-1, 4)
+        return float((np.abs(a - b) / np.maximum(np.abs(b), sig[None, :])).max())
+
+    c_orc, c_gpu = ref["costs"], gpu["costs"].astype(np.float64)
+    keep = np.isfinite(c_orc) & ~(np.abs(ref["min_gap"]) < 1e-4)
+    err = {"update": uerr(gpu["u_out"], ref["u_out"]), "warm_start": uerr(gpu["u_next"], ref["u_next"]),
+           "command": uerr(gpu["u_cmd"], ref["u_cmd"]),
+           "costs": float((np.abs(c_gpu[keep] - c_orc[keep]) / np.abs(c_orc[keep])).max()),
+           "costs_compared": int(keep.sum()), "grazing_excluded": int((~keep).sum()),
+           "tolerance": 1e-4, "effective_samples": float(1.0 / np.sum(ref["weights"] ** 2))}
+    K, N = prob["params"]["K"], prob["params"]["N"]
+    cpu = {"value": K * N / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"one full FP64 solve of the stress workload in {el:.1f} s"}
+    return err, cpu
+
+
+# ------------------------------------------------------- other sections
 
 def run_paper_point(reps=50):
     """The paper's own operating point (Table II): K=896, N=15, dt=0.1 s,
@@ -393,13 +685,13 @@ def run_paper_point(reps=50):
 
 
 def run_options(reps=30):
-    """The headline workload with each extension of the paper's method that
-    the kernel implements, one at a time: the exact quaternion angle of
-    Eq. quat_angle, control interpolation (Sec. IV-B, shift_alpha = 0.1),
-    delay compensation (Sec. IV-E, 5 ms), and the occupancy-grid collision
-    module (the 64 spheres rasterised into a 0.1 m voxel grid, 6.5 MB, used
-    alone).  Device buffers, L2 flushed before each solve, median of `reps`
-    solves timed with CUDA events."""
+    """The single-vehicle closed-loop workload with each extension of the
+    paper's method that the kernel implements, one at a time: the exact
+    quaternion angle of Eq. quat_angle, control interpolation (Sec. IV-B,
+    shift_alpha = 0.1), delay compensation (Sec. IV-E, 5 ms), and the
+    occupancy-grid collision module (the 64 spheres rasterised into a 0.1 m
+    voxel grid, 6.5 MB, used alone).  Device buffers, L2 flushed before each
+    solve, median of `reps` solves timed with CUDA events."""
     import torch
     from paper_2407_09812_gb300 import mppi
     dev = torch.device("cuda")
@@ -407,9 +699,9 @@ def run_options(reps=30):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     x, r, u, o = t(prob["x_hat"]), t(prob["ref"]), t(prob["u_nom"]), t(prob["obstacles"])
     u_out = torch.zeros(N_HEAD, 4, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    # Occupancy grid of the same spheres (inflated by nothing: the grid marks
-    # the obstacles' own volume), 0.1 m voxels over the obstacle box.
+    flush = flusher()
+    # Occupancy grid of the same spheres (the obstacles' own volume), 0.1 m
+    # voxels over the obstacle box.
     voxel, origin = 0.1, np.array([-21.0, -11.0, -1.0])
     shape = (70, 220, 420)  # (z, y, x)
     centres = [origin[a] + voxel * (np.arange(n) + 0.5) for a, n in ((2, shape[0]), (1, shape[1]), (0, shape[2]))]
@@ -453,7 +745,7 @@ def run_options(reps=30):
                              "lookup_bytes_per_s": lookups / (ms * 1e-3),
                              "note": "one 1-byte voxel read per state; the grid fits in L2"}
         out.append(entry)
-    return {"workload": WORKLOAD, "variants": out}
+    return {"workload": CLOSED_LOOP, "variants": out}
 
 
 def run_serving(args):
@@ -466,108 +758,112 @@ def run_serving(args):
     for nv in (1, 10, 100, 300):
         r = serve.run_fleet(duration_s=max(1.0, min(10.0, args.serve_seconds / 3)), n_vehicles=nv, warmup_s=0.5)
         sweep.append({k: r[k] for k in ("workload", "solves_per_s", "rollout_steps_per_s", "latency_ms",
-                                        "missed_ticks", "ticks", "mean_batch")})
+                                        "missed_ticks", "ticks", "mean_batch") if k in r})
     main["lighter_fleets"] = sweep
     return main
 
 
-def cpu_baseline(seconds: float):
-    """The FP64 oracle as it stands, OpenMP over all host cores, on solves
-    of the headline workload until about `seconds` have passed."""
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_on_fleet(probs, budget_s: float):
+    """Solves fleet instances with the FP64 oracle (OpenMP over each
+    instance's samples, all host cores), in order, until `budget_s` has
+    passed (at least one, at most all); returns (rollout-steps, solves,
+    seconds)."""
     from oracle import oracle as O
-    prob = headline_problem(0)
-    refs = reference_windows(64)
     threads = os.cpu_count() or 1
-    n, t0 = 0, time.perf_counter()
-    x, u = prob["x_hat"], prob["u_nom"]
+    steps = n = 0
+    t0 = time.perf_counter()
     while True:
-        step = dict(prob, x_hat=x, u_nom=u, ref=refs[n % 64], iter=n)
-        r = O.mppi_step(step, n_threads=threads)
-        x, u = r["x_next"].astype(np.float32), r["u_next"].astype(np.float32)
+        p = probs[n]
+        O.mppi_step(p, n_threads=threads)
+        steps += p["params"]["K"] * p["params"]["N"]
         n += 1
         el = time.perf_counter() - t0
-        if el >= seconds or n >= 1024:
-            break
-    rate = K_HEAD * N_HEAD * n / el
-    # The same oracle on one core, on a K-subsample of one solve (rollouts
-    # are independent, so rollout-steps/s scale with the sample count).
-    k1 = 1024
-    sub = dict(prob, params=dict(prob["params"], K=k1), ref=refs[0], iter=0)
-    t1 = time.perf_counter()
-    O.mppi_step(sub, n_threads=1)
-    el1 = time.perf_counter() - t1
-    rate1 = k1 * N_HEAD / el1
-    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} full solves of the headline workload (K=16384, N=100, 64 spheres) in {el:.1f} s",
-            "solves_per_s": n / el,
-            "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
-                            "sample": f"one solve of the headline workload with K subsampled to {k1} "
-                                      f"in {el1:.2f} s"},
-            "parallel_speedup": rate / rate1}
+        if el >= budget_s or n == len(probs):
+            return steps, n, el
+
+
+def cpu_baseline(seconds: float):
+    """The FP64 oracle as it stands, OpenMP over all host cores, on the
+    fleet's instances in order until about `seconds` have passed; rates are
+    rollout-steps of the instances solved per second."""
+    from paper_2407_09812_gb300 import inputs as I
+    probs = I.batched_uneven(n=N_FLEET, seed=FLEET_SEED, dt=FLEET_DT)
+    steps, n, el = oracle_on_fleet(probs, seconds)
+    return {"value": steps / el, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"the first {n} of the 256 fleet instances in order, each one full FP64 solve, in {el:.1f} s",
+            "solves_per_s": n / el}
 
 
 def reference_arm(args) -> dict:
     """The FP64 oracle as it stands, OpenMP over all host cores, as the
-    reference arm: the headline closed loop, W untimed and K timed steps,
-    each step one solve.  A solve is a bounded sample of the workload: when
-    K + W full solves would take more than about 150 s on this host, every
-    step solves the first k of the K=16384 samples instead (rollouts are
-    independent, so rollout-steps/s carry over), k stated in `sample`."""
-    from oracle import oracle as O
-    prob = headline_problem(0)
+    reference arm on the headline fleet: W untimed and K timed steps; each
+    step solves a bounded sample of the fleet, the next `per_step`
+    instances in order (wrapping), sized from one calibration solve so that
+    the whole run takes about `--ref-seconds`; rollout-steps/s are those
+    of the instances solved."""
+    from paper_2407_09812_gb300 import inputs as I
+    probs = I.batched_uneven(n=N_FLEET, seed=FLEET_SEED, dt=FLEET_DT)
     n_total = args.warmup + args.steps
-    refs = reference_windows(n_total)
-    threads = os.cpu_count() or 1
     t_all = time.perf_counter()
-    x, u = prob["x_hat"], prob["u_nom"]
-    # One full solve to size the sample.
-    t0 = time.perf_counter()
-    r = O.mppi_step(dict(prob, ref=refs[0], iter=0), n_threads=threads)
-    t_full = time.perf_counter() - t0
-    k = K_HEAD
-    if t_full * n_total > 150.0:
-        k = max(256, int(K_HEAD * 150.0 / (t_full * n_total)) // 256 * 256)
-    params = dict(prob["params"], K=k)
-    times = []
+    s0, _, e0 = oracle_on_fleet(probs, min(1.0, 0.05 * args.ref_seconds))  # calibration
+    rate = s0 / e0
+    fleet_steps = sum(p["params"]["K"] * p["params"]["N"] for p in probs)
+    fleet_s = fleet_steps / rate
+    per_step = int(max(1, min(N_FLEET, N_FLEET * args.ref_seconds / (fleet_s * n_total))))
+    times, steps_solved, at = [], [], 0
     for i in range(n_total):
-        step = dict(prob, params=params, x_hat=x, u_nom=u, ref=refs[i], iter=i)
+        from oracle import oracle as O
+        threads = os.cpu_count() or 1
         t0 = time.perf_counter()
-        r = O.mppi_step(step, n_threads=threads)
+        st = 0
+        for j in range(per_step):
+            p = probs[(at + j) % N_FLEET]
+            O.mppi_step(dict(p, iter=p["iter"] + i), n_threads=threads)
+            st += p["params"]["K"] * p["params"]["N"]
         dt = time.perf_counter() - t0
-        x, u = r["x_next"].astype(np.float32), r["u_next"].astype(np.float32)
+        at = (at + per_step) % N_FLEET
         if i >= args.warmup:
             times.append(dt)
+            steps_solved.append(st)
     times = np.array(times)
-    value = k * N_HEAD / float(times.mean())
-    sample = (f"{args.steps} timed closed-loop steps of the headline workload, each one solve with "
-              f"{'all ' if k == K_HEAD else 'the first '}{k} of the 16384 samples, after {args.warmup} untimed")
+    value = float(np.sum(steps_solved) / times.sum())
+    sample = (f"{args.steps} timed steps after {args.warmup} untimed; each step solves the next {per_step} of the "
+              f"256 fleet instances (in order, wrapping), each one full FP64 solve")
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(times.mean() * 1e3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "K": K_HEAD, "N": N_HEAD, "M": M_HEAD},
-            "impl": "reference",
+            "config": {"workload": WORKLOAD, "instances": N_FLEET},
+            "impl": "reference", "solves_per_s": per_step * len(times) / float(times.sum()),
             "latency_ms": {"p50": float(np.percentile(times, 50) * 1e3),
                            "p99": float(np.percentile(times, 99) * 1e3)},
-            "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": sample, "value": value, "unit": UNIT},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count() or 1, "sample": sample, "value": value,
+                             "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_all}
 
 
+# ------------------------------------------------------------------ main
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0, help="reference arm: oracle time for the whole run")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-vehicles", type=int, default=1000)
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sections")
-    ap.add_argument("--section", default="all", choices=["all", "batched", "stress", "serving", "paper", "options"],
-                    help="run one extra section alone and print its JSON (profiling aid)")
+    ap.add_argument("--no-extras", action="store_true", help="only the headline fleet and its end-to-end figure")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the stress workload's FP64 oracle comparison")
+    ap.add_argument("--section", default="all",
+                    choices=["all", "fleet", "closed_loop", "stress", "serving", "paper", "options", "plain"],
+                    help="run one section alone and print its JSON (profiling aid)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    world, rank, local = dist_setup(args.gpus)
+    world, rank, local = dist_setup()
     args.world = world
 
     if args.impl == "reference":
@@ -583,62 +879,78 @@ def main():
         dist.init_process_group("nccl")
     from paper_2407_09812_gb300 import build as B
     B.build()
+    from paper_2407_09812_gb300 import mppi
+    clk = ClockSampler(torch.cuda.current_device()).start()
+    peaks = mppi.measure_peaks()
 
     if args.section != "all":
-        fn = {"batched": lambda: run_batched(args), "stress": run_stress, "serving": lambda: run_serving(args),
-              "paper": run_paper_point, "options": run_options}
-        print(json.dumps({"section": args.section, **fn[args.section]()}), flush=True)
+        fn = {"fleet": lambda: run_fleet(args, rank, peaks, clk)["ms"].tolist(),
+              "closed_loop": lambda: run_closed_loop(args.steps, peaks),
+              "stress": lambda: run_stress(peaks)[0], "serving": lambda: run_serving(args),
+              "paper": run_paper_point, "options": run_options, "plain": run_plain_step}
+        out = fn[args.section]()
+        clk.stop()
+        print(json.dumps({"section": args.section, "result": out, "peaks": peaks}), flush=True)
         return
 
-    res = run_closed_loop(args, rank)
+    res = run_fleet(args, rank, peaks, clk)
+    fleet = res["fleet"]
     ms = res["ms"]
-    total_ms = float(ms.sum())
-    total_ms_max = barrier_max(total_ms, world)
-    per_step = total_ms_max / args.steps
-    steps_per_solve = K_HEAD * N_HEAD
-    value = whole_job_rate(steps_per_solve, args.steps, total_ms_max, world)
+    total_ms_max = barrier_max(float(ms.sum()), world)
+    value = whole_job_rate(fleet.rollout_steps, args.steps, total_ms_max, world)
 
     if rank != 0:
+        clk.stop()
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
-    flop_launch = steps_per_solve * FLOP_PER_STEP + res["pairs_per_solve"] * FLOP_PER_PAIR
-    achieved = flop_launch / (float(ms.mean()) * 1e-3) / 1e12
-    peak = fp32_peak_tflops()
+    mean = float(ms.mean())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "K": K_HEAD, "N": N_HEAD, "M": M_HEAD, "dt": DT_HEAD,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances": fleet.n, "rollout_steps_per_launch": fleet.rollout_steps,
+                   "sum_K": int(fleet.K.sum()), "N_range": [int(fleet.N.min()), int(fleet.N.max())],
+                   "M_range": [int(fleet.M.min()), int(fleet.M.max())],
                    "l2": "flushed between timed steps (256 MiB write outside the step's events)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "solves_per_s": world * args.steps / (total_ms_max * 1e-3),
-        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
-                       "mean": float(ms.mean())},
+        "solves_per_s": world * fleet.n * args.steps / (total_ms_max * 1e-3),
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)), "mean": mean,
+                       "note": "one persistent launch solves all 256 vehicles: a vehicle's solve latency is "
+                               "its launch's"},
         "gpu_launches": args.steps,
-        "clocks": res["clocks"],
-        "status_last_step": res["status"],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": HEADLINE_TRAFFIC_BYTES,
-                     "traffic_unit": "bytes per launch (ncu capture)",
-                     "kernel": "mppi_step_kernel",
-                     "work": {"flop_per_rollout_step": FLOP_PER_STEP, "flop_per_obstacle_pair": FLOP_PER_PAIR,
-                              "obstacle_pairs_evaluated_per_solve": res["pairs_per_solve"],
-                              "obstacle_pairs_all_per_solve": K_HEAD * (N_HEAD + 1) * M_HEAD},
-                     "peak_note": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
+        "shape": shape_dict(res["shape"]), "autotune_s": res["tune_s"],
+        "status_ok_last_step": res["status_ok"], "state_finite": res["finite"],
+        "roofline": roofline(fleet.rollout_steps * FLOP_PER_STEP + res["pairs"] * FLOP_PER_PAIR,
+                             mufu_ops(fleet.rollout_steps, res["pairs"]), mean, peaks, captured_traffic("fleet"),
+                             "batched launch of 256 uneven instances"),
+        "obstacle_pairs": {"evaluated_per_launch": res["pairs"],
+                           "all_per_launch": int((fleet.K * (fleet.N + 1) * fleet.M).sum())},
+        "peaks": {"fp32_tflops": peaks["fp32_flops"] / 1e12, "sm_count": peaks["sm_count"],
+                  **{k: v / 1e9 for k, v in peaks.items() if k.endswith("_ops")}, "mufu_unit": "Gop/s"},
     }
-    line["e2e"] = run_e2e(args, rank, n_steps=min(args.steps, 100))
+    line["e2e"] = run_fleet_e2e(args, fleet, res["shape"], n_steps=min(args.steps, 50))
+    stress_in = None
     if not args.no_extras:
-        line["batched"] = run_batched(args)
-        line["stress"] = run_stress()
+        line["plain"] = {"plain_step": run_plain_step(), "one_by_one": run_one_by_one(fleet)}
+        line["plain"]["batched_over_one_by_one"] = (value / world) / line["plain"]["one_by_one"]["rollout_steps_per_s"]
+        line["closed_loop"] = run_closed_loop(max(args.steps, 100), peaks)
+        line["stress"], prob, gpu = run_stress(peaks)
+        stress_in = (prob, gpu)
         line["paper_operating_point"] = run_paper_point()
         line["options"] = run_options()
         try:
             line["serving"] = run_serving(args)
         except (ImportError, AttributeError, OSError) as e:
             line["serving"] = {"unavailable": str(e)[:200]}
+    clk.stop()
+    line["clocks"] = clk.summary()
+    line["clocks"]["window"] = "every 100 ms from before the first GPU section to the end of the last"
+    line["clocks"]["headline_samples"] = clk.summary(*res["window"])["samples"]
     line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if stress_in and not args.no_oracle:
+        line["stress"]["oracle_err"], line["stress"]["cpu_baseline"] = stress_oracle_error(*stress_in)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

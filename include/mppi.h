@@ -227,6 +227,23 @@ int mppi_solve_batch(mppi_handle h, const mppi_instance* instances, int32_t n, v
  * are updated in place between replays. */
 int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_t n, void* stream);
 
+/* The batched step with HOST buffers, synchronous (the batched form of
+ * mppi_solve; Alg. 1, one step per vehicle).  `instances` is a HOST array of
+ * n descriptors whose pointers are all HOST pointers; iter_dev must be NULL
+ * (the counter is `iter`).  The inputs of all instances are packed, in
+ * instance order, into one pinned block of 16-byte aligned segments per
+ * instance (x_hat[13] padded to 16, ref[(N+1)*13] padded to a multiple of 4,
+ * obstacles[M*4], u_nom[N*4]) and copied in with one copy; the launch is
+ * that of mppi_solve_batch_graph; the outputs (per instance u_out[N*4],
+ * u_cmd[4], u_next[N*4], x_next[13] padded to 16, status padded to 4, then
+ * costs[K] padded to a multiple of 4 when costs != NULL) come back with one
+ * copy and are written to the non-NULL output pointers.  An output buffer
+ * may be an input buffer (u_next == u_nom for an in-place warm start).
+ * Returns MPPI_EINVAL (nothing written), MPPI_ENOMEM, MPPI_ECUDA, or the
+ * first non-OK per-instance status in instance order (each instance's
+ * `status`, when non-NULL, receives its own). */
+int mppi_solve_batch_host(mppi_handle h, const mppi_instance* instances, int32_t n);
+
 /* Measurement hook (the paper has no counterpart): with a DEVICE counter
  * set, every later launch of the handle adds to counters[0] the number of
  * (rollout state, obstacle) pairs it evaluated after its exact culling
@@ -234,6 +251,26 @@ int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_
  * counts as zero, and that cannot be in collision are skipped).  Used to state the roofline in work actually
  * required.  NULL turns it off.  The counter must be 8-byte aligned. */
 int mppi_set_counters(mppi_handle h, uint64_t* counters);
+
+/* Measured throughput of the pipes the step is bound by (the paper has no
+ * counterpart): FP32 fused multiply-add and the multi-function unit, each
+ * the best of a few launches of a micro-benchmark that fills every SM. */
+typedef struct {
+    int32_t sm_count;   /* SMs of the current device                      */
+    int32_t reserved;
+    double fp32_flops;  /* FFMA rate, 2 flop per FMA [flop/s]             */
+    double fp32_ms;     /* duration of the timed FFMA launch [ms]         */
+    double ex2_ops;     /* ex2.approx results per second                  */
+    double lg2_ops;     /* lg2.approx                                     */
+    double rsqrt_ops;   /* rsqrt.approx                                   */
+    double sin_ops;     /* sin.approx                                     */
+    double cos_ops;     /* cos.approx                                     */
+} mppi_peaks;
+
+/* Runs the micro-benchmark on the current device and `stream`
+ * (synchronous, about 30 ms; allocates a small scratch buffer).  Used to
+ * state the roofline against rates measured on the GPU itself. */
+int mppi_measure_peaks(mppi_peaks* out, void* stream);
 
 /* Failure-path hook (the paper has no counterpart).  Every device-side wait
  * of the kernel (the obstacle staging copy, the pipelined form's state
@@ -283,6 +320,16 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
  * synthetic problem: the best shape depends on how the obstacles lie
  * relative to the rollouts, which a synthetic problem does not reproduce. */
 int mppi_autotune_instance(mppi_handle h, const mppi_instance* instance, mppi_shape* best, void* stream);
+
+/* The same tuning on a whole batch of the caller's instances (DEVICE
+ * buffers, as for mppi_solve_batch; the paper has no counterpart): every
+ * candidate shape, then the obstacle tiling of the fastest, is timed as
+ * one persistent batched launch of these instances (outputs not written,
+ * Philox counters not advanced), and the fastest is stored for the key a
+ * batch of these instances is looked up under (its mean K, largest N and
+ * largest M).  Synchronous. */
+int mppi_autotune_batch(mppi_handle h, const mppi_instance* instances, int32_t n, mppi_shape* best,
+                        void* stream);
 
 /* Looks up the shape the handle uses for a problem of size (K, N, M)
  * (the paper has no counterpart). */

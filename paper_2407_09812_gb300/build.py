@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libmppi_gb300.so")
-SOURCES = ["mppi_kernels.cu", "mppi_abi.cu", "mppi_server.cu", "mppi_noalloc.cu"]
+SOURCES = ["mppi_kernels.cu", "mppi_abi.cu", "mppi_server.cu", "mppi_noalloc.cu", "mppi_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -169,6 +169,10 @@ struct mppi_ctx {
     float* d_io = nullptr;
     float* h_io = nullptr;
     size_t io_floats = 0;
+    // mppi_solve_batch_host's packed blocks (pinned host, device).
+    float* d_bio = nullptr;
+    float* h_bio = nullptr;
+    size_t bio_floats = 0;
     // mppi_solve replayed from a graph [copy in, kernel, copy out], keyed by
     // everything the captured launch depends on.
     GraphEntry io_graph;
@@ -391,19 +395,22 @@ int plan_batch(mppi_ctx* h, const mppi_instance* ins, int n, BatchPlan* plan) {
     if (rc) return rc;
     if (!h->h_ntiles && cudaMallocHost(&h->h_ntiles, sizeof(int)) != cudaSuccess) return MPPI_ENOMEM;
     size_t off = 0;
-    std::vector<std::pair<float, int2>> order;
-    order.reserve((size_t)tiles);
+    // Longest tiles first: every tile of an instance has the same estimated
+    // cost, so the instances are ordered (stable, descending) and each one's
+    // tiles follow in ascending order.
+    std::vector<std::pair<float, int>> order((size_t)n);
     for (int i = 0; i < n; ++i) {
         DevInstance d = make_instance(h, ins[i], s);
         d.part_off = (long long)off;
         off += (size_t)d.n_tiles * partial_stride(ins[i].N);
         h->h_insts[i] = d;
-        const float w = (float)ins[i].N * (1.0f + ins[i].M / 8.0f);
-        for (int t = 0; t < d.n_tiles; ++t) order.push_back({w, make_int2(i, t)});
+        order[(size_t)i] = {(float)ins[i].N * (1.0f + ins[i].M / 8.0f), i};
     }
     std::stable_sort(order.begin(), order.end(),
-                     [](const std::pair<float, int2>& x, const std::pair<float, int2>& y) { return x.first > y.first; });
-    for (size_t t = 0; t < order.size(); ++t) h->h_tilemap[t] = order[t].second;
+                     [](const std::pair<float, int>& x, const std::pair<float, int>& y) { return x.first > y.first; });
+    size_t t_out = 0;
+    for (const auto& o : order)
+        for (int t = 0; t < h->h_insts[o.second].n_tiles; ++t) h->h_tilemap[t_out++] = make_int2(o.second, t);
     *h->h_ntiles = (int)tiles;
     plan->n_tiles = (int)tiles;
     plan->N_b = bucket_pow2(Nmax, 16);
@@ -446,6 +453,19 @@ int persistent_grid(Shape s, size_t smem) { return sm_count() * max_active_block
 
 }  // namespace
 
+// Candidate launch shapes of the autotuners: one thread or 2/4/8/32 lanes
+// per sample (blocks 64-512, at least 8 samples per block), and the
+// pipelined form with one or two cost lanes per sample.
+static std::vector<Shape> tuning_candidates() {
+    std::vector<Shape> cands;
+    for (int b : {64, 128, 256, 512})
+        for (int l : {1, 2, 4, 8, 32})
+            if (b / l >= 8) cands.push_back(Shape{b, l, 0, 0.0f});
+    for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 1, 0.0f});
+    for (int b : {192, 384}) cands.push_back(Shape{b, 2, 1, 0.0f});
+    return cands;
+}
+
 // Times every candidate shape on one instance (outputs not written) and
 // stores the fastest in the handle's table for the instance's size bucket.
 static int tune_on(mppi_ctx* h, mppi_instance in, cudaStream_t st, mppi_shape* best) {
@@ -459,12 +479,7 @@ static int tune_on(mppi_ctx* h, mppi_instance in, cudaStream_t st, mppi_shape* b
     // at least 8 samples per block), and the pipelined form with one or two
     // cost lanes per sample; then, for the fastest of those, the obstacle
     // tiling (the margin of the warps' kept-obstacle lists).
-    std::vector<Shape> cands;
-    for (int b : {64, 128, 256, 512})
-        for (int l : {1, 2, 4, 8, 32})
-            if (b / l >= 8) cands.push_back(Shape{b, l, 0, 0.0f});
-    for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 1, 0.0f});
-    for (int b : {192, 384}) cands.push_back(Shape{b, 2, 1, 0.0f});
+    const std::vector<Shape> cands = tuning_candidates();
     Shape bestS{128, 1, 0, 0.0f};
     float bestT = 1e30f;
     int rc = MPPI_OK;
@@ -589,6 +604,8 @@ void mppi_destroy(mppi_handle h) {
     cudaFree(h->d_insts);
     cudaFree(h->d_tilemap);
     cudaFree(h->d_io);
+    cudaFree(h->d_bio);
+    if (h->h_bio) cudaFreeHost(h->h_bio);
     if (h->h_insts) cudaFreeHost(h->h_insts);
     if (h->h_tilemap) cudaFreeHost(h->h_tilemap);
     if (h->h_ntiles) cudaFreeHost(h->h_ntiles);
@@ -873,6 +890,107 @@ int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_
     return cudaGraphLaunch(it->second.exec, st) == cudaSuccess ? MPPI_OK : MPPI_ECUDA;
 }
 
+// Host-buffer batch: the inputs of every instance are packed, in instance
+// order, into one pinned block (16-byte aligned segments: x_hat, ref,
+// obstacles, u_nom), copied in with one copy and solved by the graph-replayed
+// batched launch; the outputs (u_out, u_cmd, u_next, x_next, status, then
+// costs when asked for) come back with one copy and are unpacked.
+int mppi_solve_batch_host(mppi_handle h, const mppi_instance* instances, int32_t n) {
+    if (!h || !instances || n < 1) return MPPI_EINVAL;
+    auto up4 = [](size_t v) { return (v + 3) / 4 * 4; };
+    size_t in_f = 0, out_f = 0;
+    for (int i = 0; i < n; ++i) {
+        const mppi_instance& in = instances[i];
+        int rc = check_step(in.K, in.N, in.dt, in.lambda, in.sigma);
+        if (rc) return rc;
+        if (in.M < 0 || in.M > MPPI_M_MAX || in.reserved != 0 || in.iter_dev) return MPPI_EINVAL;
+        if (!in.x_hat || !in.ref || !in.u_nom || (in.M > 0 && !in.obstacles)) return MPPI_EINVAL;
+        const size_t N = (size_t)in.N;
+        in_f += 16 + up4(13 * (N + 1)) + 4 * (size_t)in.M + 4 * N;
+        out_f += 8 * N + 24 + (in.costs ? up4((size_t)in.K) : 0);
+    }
+    const size_t total = in_f + out_f;
+    cudaStream_t st = h->stream;
+    if (total > h->bio_floats || !h->h_bio) {
+        if (h->h_bio) cudaFreeHost(h->h_bio);
+        if (h->d_bio) cudaFree(h->d_bio);
+        h->h_bio = nullptr;
+        h->d_bio = nullptr;
+        h->bio_floats = 0;
+        const size_t n_alloc = std::max(total, (size_t)(1.25 * (double)total));
+        if (cudaMallocHost(&h->h_bio, n_alloc * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&h->d_bio, n_alloc * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return MPPI_ENOMEM;
+        }
+        h->bio_floats = n_alloc;
+    }
+    float* hb = h->h_bio;
+    float* db = h->d_bio;
+    std::vector<mppi_instance> dev((size_t)n);
+    size_t oi = 0, oo = in_f;
+    for (int i = 0; i < n; ++i) {
+        const mppi_instance& in = instances[i];
+        const size_t N = (size_t)in.N, M = (size_t)in.M;
+        mppi_instance& d = dev[(size_t)i];
+        d = in;
+        std::memcpy(hb + oi, in.x_hat, 13 * sizeof(float));
+        d.x_hat = db + oi;
+        oi += 16;
+        std::memcpy(hb + oi, in.ref, 13 * (N + 1) * sizeof(float));
+        d.ref = db + oi;
+        oi += up4(13 * (N + 1));
+        if (M > 0) std::memcpy(hb + oi, in.obstacles, 4 * M * sizeof(float));
+        d.obstacles = M > 0 ? db + oi : nullptr;
+        oi += 4 * M;
+        std::memcpy(hb + oi, in.u_nom, 4 * N * sizeof(float));
+        d.u_nom = db + oi;
+        oi += 4 * N;
+        d.u_out = db + oo;
+        d.u_cmd = db + oo + 4 * N;
+        d.u_next = db + oo + 4 * N + 4;
+        d.x_next = db + oo + 8 * N + 4;
+        d.status = reinterpret_cast<int32_t*>(db + oo + 8 * N + 20);
+        oo += 8 * N + 24;
+        d.costs = in.costs ? db + oo : nullptr;
+        if (in.costs) oo += up4((size_t)in.K);
+    }
+    if (cudaMemcpyAsync(db, hb, in_f * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) return MPPI_ECUDA;
+    int rc = mppi_solve_batch_graph(h, dev.data(), n, st);
+    if (rc) {
+        cudaStreamSynchronize(st);
+        return rc;
+    }
+    if (cudaMemcpyAsync(hb + in_f, db + in_f, out_f * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaEventRecord(h->ev_io, st) != cudaSuccess)
+        return MPPI_ECUDA;
+    cudaError_t q;
+    while ((q = cudaEventQuery(h->ev_io)) == cudaErrorNotReady) {
+    }
+    if (q != cudaSuccess) return MPPI_ECUDA;
+    int first = MPPI_OK;
+    oo = in_f;
+    for (int i = 0; i < n; ++i) {
+        const mppi_instance& in = instances[i];
+        const size_t N = (size_t)in.N;
+        const float* o = hb + oo;
+        if (in.u_out) std::memcpy(in.u_out, o, 4 * N * sizeof(float));
+        if (in.u_cmd) std::memcpy(in.u_cmd, o + 4 * N, 4 * sizeof(float));
+        if (in.u_next) std::memcpy(in.u_next, o + 4 * N + 4, 4 * N * sizeof(float));
+        if (in.x_next) std::memcpy(in.x_next, o + 8 * N + 4, 13 * sizeof(float));
+        int32_t status;
+        std::memcpy(&status, o + 8 * N + 20, sizeof(status));
+        if (in.status) *in.status = status;
+        if (status != MPPI_OK && first == MPPI_OK) first = status;
+        oo += 8 * N + 24;
+        if (in.costs) {
+            std::memcpy(in.costs, hb + oo, (size_t)in.K * sizeof(float));
+            oo += up4((size_t)in.K);
+        }
+    }
+    return first;
+}
+
 int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* best, void* stream) {
     if (!h || K < 1 || K > MPPI_K_MAX || N < 1 || N > MPPI_N_MAX || M < 0 || M > MPPI_M_MAX) return MPPI_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -916,6 +1034,81 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
     const int rc = tune_on(h, in, st, best);
     cudaFree(d);
     return rc;
+}
+
+int mppi_autotune_batch(mppi_handle h, const mppi_instance* instances, int32_t n, mppi_shape* best,
+                        void* stream) {
+    if (!h || !instances || n < 1) return MPPI_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<mppi_instance> ins(instances, instances + n);
+    long long sumK = 0;
+    int Nmax = 1, Mmax = 0;
+    for (auto& in : ins) {
+        int rc = check_instance(in, h);
+        if (rc) return rc;
+        in.u_out = in.u_cmd = in.u_next = in.x_next = in.costs = nullptr;
+        in.status = nullptr;
+        in.iter_dev = nullptr;
+        sumK += in.K;
+        Nmax = std::max(Nmax, in.N);
+        Mmax = std::max(Mmax, in.M);
+    }
+    const Shape saved = h->forced;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Shape bestS{128, 1, 0, 0.0f};
+    float bestT = 1e30f;
+    int rc = MPPI_OK;
+    auto time_shape = [&](const Shape& s) {
+        h->forced = s;
+        if ((rc = mppi_solve_batch(h, ins.data(), n, st))) {
+            // A shape whose shared memory does not fit is skipped.
+            if (rc == MPPI_EINVAL) rc = MPPI_OK;
+            return;
+        }
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) mppi_solve_batch(h, ins.data(), n, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = MPPI_ECUDA;
+            return;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < bestT) {
+            bestT = ms;
+            bestS = s;
+        }
+    };
+    for (const Shape& s : tuning_candidates()) {
+        time_shape(s);
+        if (rc) break;
+    }
+    if (!rc && Mmax > 0) {
+        const Shape base = bestS;
+        for (float m : {0.25f, 0.5f, 1.0f, 2.0f}) {
+            if (m == list_margin(base)) continue;
+            Shape s = base;
+            s.margin = m;
+            time_shape(s);
+            if (rc) break;
+        }
+    }
+    h->forced = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    if (rc) return rc;
+    // The key a batch of these instances looks its shape up under.
+    h->table[bucket_key(sumK / n, Nmax, Mmax)] = bestS;
+    if (best) {
+        best->block = bestS.block;
+        best->lanes = bestS.lanes;
+        best->pipelined = bestS.pipe;
+        best->list_margin = list_margin(bestS);
+    }
+    return MPPI_OK;
 }
 
 int mppi_autotune_instance(mppi_handle h, const mppi_instance* instance, mppi_shape* best, void* stream) {

@@ -327,7 +327,9 @@ def batched_uneven(n=256, seed=2, dt=0.01, K_range=(1024, 32768), N_range=(30, 1
         x[0:3] += rng.uniform(-1.0, 1.0, 3).astype(np.float32)
         x[7:10] += rng.normal(0.0, 0.5, 3).astype(np.float32)
         obs = spheres(rng, M, (-20.0, -10.0, 0.0), (20.0, 10.0, 5.0), 0.3, 1.0)
-        probs.append(problem(m, p, x, ref, obs, hover_u(m, N), it=int(rng.integers(0, 1 << 20))))
+        prob = problem(m, p, x, ref, obs, hover_u(m, N), it=int(rng.integers(0, 1 << 20)))
+        prob["phase"] = phase  # the reference's figure-eight phase (for later windows)
+        probs.append(prob)
     return probs
 
 

@@ -54,6 +54,17 @@ class Instance(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+# The descriptor as a numpy record (same layout), so that a fleet's
+# descriptors can be filled with vectorised operations.
+INSTANCE_DTYPE = np.dtype(Instance)
+
+
+class Peaks(C.Structure):
+    _fields_ = [("sm_count", C.c_int32), ("reserved", C.c_int32), ("fp32_flops", C.c_double),
+                ("fp32_ms", C.c_double), ("ex2_ops", C.c_double), ("lg2_ops", C.c_double),
+                ("rsqrt_ops", C.c_double), ("sin_ops", C.c_double), ("cos_ops", C.c_double)]
+
+
 class Shape(C.Structure):
     _fields_ = [("block", C.c_int32), ("lanes", C.c_int32), ("pipelined", C.c_int32), ("list_margin", C.c_float)]
 
@@ -105,10 +116,13 @@ def lib():
                                    _VP]
     L.mppi_solve_batch.argtypes = [_VP, C.POINTER(Instance), C.c_int32, _VP]
     L.mppi_solve_batch_graph.argtypes = [_VP, C.POINTER(Instance), C.c_int32, _VP]
+    L.mppi_solve_batch_host.argtypes = [_VP, _VP, C.c_int32]
+    L.mppi_measure_peaks.argtypes = [C.POINTER(Peaks), _VP]
     L.mppi_set_shape.argtypes = [_VP, C.POINTER(Shape)]
     L.mppi_get_shape.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape)]
     L.mppi_autotune.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape), _VP]
     L.mppi_autotune_instance.argtypes = [_VP, C.POINTER(Instance), C.POINTER(Shape), _VP]
+    L.mppi_autotune_batch.argtypes = [_VP, C.POINTER(Instance), C.c_int32, C.POINTER(Shape), _VP]
     L.mppi_solve_noalloc.argtypes = [C.POINTER(Model), C.POINTER(Params), _VP, _VP, _VP, C.c_int32, _VP, C.c_uint64,
                                      _VP, _VP, _VP, _VP, _VP, _VP, _VP]
     if hasattr(L, "mppi_server_create"):
@@ -379,10 +393,48 @@ class Solver:
         """mppi_solve_batch(_graph): instances are dicts of torch CUDA tensors
         (x_hat, ref, obstacles, u_nom, and any of u_out, u_cmd, u_next,
         x_next, costs, status, iter_dev) plus K, N, dt, lambda, sigma, seed,
-        stream_id, iter."""
-        arr = self._instances(instances)
+        stream_id, iter; or a record array of INSTANCE_DTYPE holding device
+        addresses."""
+        if isinstance(instances, np.ndarray):
+            # A record array of INSTANCE_DTYPE with device addresses, passed
+            # as is (no per-buffer size checks: the caller sized them).
+            if instances.dtype != INSTANCE_DTYPE or not instances.flags.c_contiguous:
+                raise ValueError("instances must be a contiguous record array of INSTANCE_DTYPE")
+            arr, n = C.cast(instances.ctypes.data, C.POINTER(Instance)), instances.size
+        else:
+            arr, n = self._instances(instances), len(instances)
         fn = lib().mppi_solve_batch_graph if graph else lib().mppi_solve_batch
-        _check(fn(self.h, arr, len(instances), _stream_ptr(stream)), "mppi_solve_batch")
+        _check(fn(self.h, arr, n, _stream_ptr(stream)), "mppi_solve_batch")
+
+    def solve_batch_host(self, instances) -> int:
+        """mppi_solve_batch_host: a numpy record array of INSTANCE_DTYPE whose
+        pointer fields hold HOST addresses (inputs and outputs), solved
+        synchronously; returns the first non-OK instance status (or OK) and
+        raises on invalid arguments or a CUDA failure.  The caller keeps the
+        addressed arrays alive and sized for each instance's K, N and M."""
+        arr = np.ascontiguousarray(instances)
+        if arr.dtype != INSTANCE_DTYPE:
+            raise ValueError("instances must be a record array of INSTANCE_DTYPE")
+        rc = lib().mppi_solve_batch_host(self.h, arr.ctypes.data, arr.size)
+        if rc not in (OK, ENONFINITE, ETIMEOUT):
+            raise MppiError(rc, "mppi_solve_batch_host")
+        return rc
+
+    def autotune_batch(self, instances: list, stream=None):
+        """mppi_autotune_batch: the fastest shape for one persistent launch
+        of these instances (dicts as for solve_batch; outputs not written)."""
+        s = Shape()
+        arr = self._instances(instances)
+        _check(lib().mppi_autotune_batch(self.h, arr, len(instances), C.byref(s), _stream_ptr(stream)),
+               "mppi_autotune_batch")
+        return s.block, s.lanes, s.pipelined, s.list_margin
+
+    def batch_shape(self, instances: list):
+        """(block, lanes, pipelined, list_margin) a batched launch of these
+        instances uses."""
+        K = sum(int(d["K"]) for d in instances) // len(instances)
+        return self.get_shape(K, max(int(d["N"]) for d in instances),
+                              max(_obstacle_count(d.get("obstacles")) for d in instances))
 
     # ---------------------------------------------------------- launch shape
     def set_shape(self, block: int = 0, lanes: int = 0, pipelined: int = 0, list_margin: float = 0.0):
@@ -427,6 +479,44 @@ def solve_noalloc(model: dict, params: dict, x_hat, ref, obstacles, u_nom, it: i
                                   M, _dptr(u_nom), int(it), _dptr(u_out), _dptr(u_cmd), _dptr(u_next),
                                   _dptr(x_next), _dptr(costs), _dptr(status, "int32"), _stream_ptr(stream))
     _check(rc, "mppi_solve_noalloc")
+
+
+def host_instances(instances: list) -> np.ndarray:
+    """A record array of INSTANCE_DTYPE for mppi_solve_batch_host from dicts
+    of numpy float32 arrays (x_hat, ref, obstacles, u_nom, and any of u_out,
+    u_cmd, u_next, x_next, costs; status an int32 array) plus K, N, dt,
+    lambda, sigma, seed, stream_id, iter.  Every array is checked against
+    its instance's K and N; the caller keeps the arrays alive."""
+    arr = np.zeros(len(instances), INSTANCE_DTYPE)
+    for i, d in enumerate(instances):
+        K, N = int(d["K"]), int(d["N"])
+        _check_sizes(K, N, {f: d.get(f) for f in _sizes(1, 1) if f != "iter_dev"})
+        for f in ("x_hat", "ref", "u_nom", "u_out", "u_cmd", "u_next", "x_next", "costs", "status"):
+            a = d.get(f)
+            if a is None:
+                continue
+            want = np.int32 if f == "status" else np.float32
+            if not isinstance(a, np.ndarray) or a.dtype != want or not a.flags.c_contiguous:
+                raise ValueError(f"{f}: expected a contiguous numpy {np.dtype(want).name} array")
+            arr[f][i] = a.ctypes.data
+        obs = d.get("obstacles")
+        M = _obstacle_count(obs)
+        if M:
+            if obs.dtype != np.float32 or not obs.flags.c_contiguous:
+                raise ValueError("obstacles: expected a contiguous numpy float32 array")
+            arr["obstacles"][i] = obs.ctypes.data
+        arr["iter"][i], arr["K"][i], arr["N"][i], arr["M"][i] = int(d.get("iter", 0)), K, N, M
+        arr["dt"][i], arr["lam"][i], arr["sigma"][i] = float(d["dt"]), float(d["lambda"]), list(d["sigma"])
+        arr["seed"][i], arr["stream_id"][i] = int(d.get("seed", 0)), int(d.get("stream_id", 0))
+    return arr
+
+
+def measure_peaks(stream=None) -> dict:
+    """mppi_measure_peaks: measured FP32 FMA and MUFU throughput of the
+    current device."""
+    p = Peaks()
+    _check(lib().mppi_measure_peaks(C.byref(p), _stream_ptr(stream)), "mppi_measure_peaks")
+    return {f: getattr(p, f) for f, _ in Peaks._fields_ if f != "reserved"}
 
 
 def version() -> str:

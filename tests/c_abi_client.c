@@ -56,6 +56,10 @@ static void layout(void) {
     F(mppi_server_stats, submitted); F(mppi_server_stats, completed); F(mppi_server_stats, rejected);
     F(mppi_server_stats, batches); F(mppi_server_stats, instances); F(mppi_server_stats, bytes_in_use);
     F(mppi_server_stats, bytes_budget); F(mppi_server_stats, busy_us);
+    S(mppi_peaks);
+    F(mppi_peaks, sm_count); F(mppi_peaks, reserved); F(mppi_peaks, fp32_flops); F(mppi_peaks, fp32_ms);
+    F(mppi_peaks, ex2_ops); F(mppi_peaks, lg2_ops); F(mppi_peaks, rsqrt_ops); F(mppi_peaks, sin_ops);
+    F(mppi_peaks, cos_ops);
 }
 
 static int read_all(FILE* f, void* p, size_t n) { return fread(p, 1, n, f) == n; }

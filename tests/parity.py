@@ -65,6 +65,10 @@ def compare_step(prob, gpu: dict, orc: dict, check_costs=True):
         "u_next": control_err(gpu["u_next"], orc["u_next"], sigma),
         "u_cmd": control_err(gpu["u_cmd"], orc["u_cmd"], sigma),
         "x_next": state_err(gpu["x_next"], plant_step_of(prob, u_out[0])),
+        # Reported, not asserted: the plant step of the GPU's command against
+        # the oracle's plant step of its own command (carries the update's
+        # allowed error through one step of the model).
+        "x_next_vs_oracle": state_err(gpu["x_next"], orc["x_next"]),
     }
     if check_costs and gpu.get("costs") is not None:
         out["costs"], out["grazing"] = cost_err(gpu["costs"], orc["costs"], orc.get("min_gap"))

@@ -67,6 +67,8 @@ def test_host_validation_rejects_bad_arguments(built):
     assert L.mppi_create(None, None, None, C.byref(h)) == mppi.EINVAL
     assert L.mppi_solve(None, None, None, None, 0, None, 0, None, None, None, None, None) == mppi.EINVAL
     assert L.mppi_solve_batch(None, None, 0, None) == mppi.EINVAL
+    assert L.mppi_solve_batch_host(None, None, 0) == mppi.EINVAL
+    assert L.mppi_measure_peaks(None, None) == mppi.EINVAL
     assert L.mppi_set_wait_limit(None, 0, 0) == mppi.EINVAL
     assert mppi.strerror(mppi.ENONFINITE) == "every rollout cost was non-finite"
 
@@ -117,7 +119,7 @@ def test_c_client_compiles_and_struct_layouts_match_the_binding(tmp_path):
     out = subprocess.run([exe, "layout"], capture_output=True, text=True, check=True).stdout.split("\n")
     mirrors = {"mppi_model": mppi.Model, "mppi_params": mppi.Params, "mppi_capacity": mppi.Capacity,
                "mppi_instance": mppi.Instance, "mppi_shape": mppi.Shape, "mppi_server_cfg": mppi.ServerCfg,
-               "mppi_result": mppi.Result, "mppi_server_stats": mppi.ServerStats}
+               "mppi_result": mppi.Result, "mppi_server_stats": mppi.ServerStats, "mppi_peaks": mppi.Peaks}
     seen = set()
     for line in filter(None, out):
         struct, field, off, size = line.split()

@@ -192,3 +192,78 @@ def test_batch_of_one_and_empty_obstacle_sets(M, orc, inp):
         for k in ("u_out", "u_cmd", "u_next", "x_next", "costs"):
             assert np.array_equal(_host(a)[k], b[k]), k
         s.close()
+
+
+def test_host_buffer_batch_matches_device_batch(M, orc, inp):
+    """mppi_solve_batch_host (host buffers packed into one pinned block, one
+    copy each way, graph-replayed launch) gives bitwise the device-buffer
+    batch's results, per instance, and the oracle's; an in-place warm start
+    (u_next == u_nom) works on host buffers, and a second call of other
+    sizes reuses the packed blocks."""
+    import torch
+    probs = _uneven(inp, n=9, seed=13)
+    s = M.Solver(probs[0]["model"], probs[0]["params"], _cap(probs))
+    s.set_shape(128, 1, 0)
+    insts = [_device(p, torch) for p in probs]
+    s.solve_batch(insts, graph=True)
+    torch.cuda.synchronize()
+    want = [_host(d) for d in insts]
+    host = []
+    for p in probs:
+        K, N = p["params"]["K"], p["params"]["N"]
+        host.append({"x_hat": p["x_hat"].copy(), "ref": p["ref"].copy(), "u_nom": p["u_nom"].copy(),
+                     "obstacles": p["obstacles"].copy() if p["obstacles"].size else None,
+                     "u_out": np.zeros((N, 4), np.float32), "u_cmd": np.zeros(4, np.float32),
+                     "u_next": np.zeros((N, 4), np.float32), "x_next": np.zeros(13, np.float32),
+                     "costs": np.zeros(K, np.float32), "status": np.full(1, -99, np.int32), "K": K, "N": N,
+                     "dt": p["params"]["dt"], "lambda": p["params"]["lambda"], "sigma": p["params"]["sigma"],
+                     "seed": p["params"]["seed"], "stream_id": p["params"]["stream_id"], "iter": p["iter"]})
+    assert s.solve_batch_host(M.host_instances(host)) == M.OK
+    for p, h, w in zip(probs, host, want):
+        assert int(h["status"][0]) == 0
+        for k in ("u_out", "u_cmd", "u_next", "x_next", "costs"):
+            assert np.array_equal(h[k], w[k]), (k, p["params"]["K"], p["params"]["N"])
+        assert_step_close(p, dict(h, status=0), orc.mppi_step(p, n_threads=8))
+    # In place, fewer instances, no costs: u_next overwrites the nominal.
+    sub = host[2:6]
+    for h in sub:
+        h["u_next"] = h["u_nom"]
+        h["costs"] = None
+    nominal = [h["u_nom"].copy() for h in sub]
+    assert s.solve_batch_host(M.host_instances(sub)) == M.OK
+    for h, w, u0 in zip(sub, want[2:6], nominal):
+        assert np.array_equal(h["u_nom"], w["u_next"])
+        assert not np.array_equal(h["u_nom"], u0)
+    s.close()
+
+
+def test_batch_autotuner_times_the_batch_and_leaves_it_untouched(M, orc, inp):
+    """mppi_autotune_batch times each candidate shape as one persistent
+    launch of the caller's batch: it stores a supported shape under the
+    batch's key, writes no output and advances no device counter, and the
+    tuned batch still matches the oracle."""
+    import torch
+    probs = _uneven(inp, n=8, seed=17)
+    s = M.Solver(probs[0]["model"], probs[0]["params"], _cap(probs))
+    insts = [_device(p, torch) for p in probs]
+    sentinel = [torch.full_like(d["u_out"], 777.0) for d in insts]
+    for d, z in zip(insts, sentinel):
+        d["u_out"].copy_(z)
+    it = torch.tensor([probs[0]["iter"]], dtype=torch.int64, device="cuda")
+    insts[0]["iter_dev"] = it
+    best = s.autotune_batch(insts)
+    torch.cuda.synchronize()
+    assert all(torch.equal(d["u_out"], z) for d, z in zip(insts, sentinel))
+    assert int(it.item()) == probs[0]["iter"]
+    if best[2] == 0:
+        assert best[0] in (64, 128, 256, 512) and best[1] in (1, 2, 4, 8, 32)
+    else:
+        assert best[1] in (1, 2) and best[0] % (32 * (1 + best[1])) == 0
+    assert s.batch_shape(insts) == best
+    insts[0]["iter_dev"] = None
+    s.solve_batch(insts, graph=True)
+    torch.cuda.synchronize()
+    for p, d in zip(probs, insts):
+        assert_step_close(p, _host(d), orc.mppi_step(p, n_threads=8))
+    s.close()
+    print("autotune_batch", best)

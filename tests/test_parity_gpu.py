@@ -1,15 +1,15 @@
 """CUDA path against the FP64 oracle, element by element, through the C ABI.
 
 Sizes span several tiles and a ragged tail; the full-size configurations
-(closed loop K=16384 N=100 M=64; stress K=262144 N=200 M=1024) are checked
-on every output the oracle can compute at that size (all costs and the
-update for the closed loop; sampled costs plus the update identity for the
-stress case).
+(closed loop K=16384 N=100 M=64; stress K=262144 N=200 M=1024; the ABI's
+limits) are checked on every output against a full FP64 oracle step.
 """
+import os
+
 import numpy as np
 import pytest
 
-from parity import COST_RTOL, U_RTOL, assert_step_close, compare_step, control_err, cost_err
+from parity import assert_step_close, cost_err
 
 pytestmark = pytest.mark.gpu
 
@@ -178,56 +178,34 @@ def test_closed_loop_full_size(M, orc, inp):
     print("closed loop worst", worst)
 
 
-def test_stress_full_size_sampled(M, orc, inp):
-    """K=262144, N=200, dt=0.005, 512 spheres + 512 pillars: sampled costs
-    against the oracle, and the update equals sum_k w_k delta_k with the
-    weights of the GPU's own costs (FP64) and the oracle's noise."""
+def test_stress_full_size(M, orc, inp):
+    """K=262144, N=200, dt=0.005, 512 spheres + 512 pillars: every
+    per-sample cost, the updated nominal, the warm start and the command
+    against one full FP64 oracle step on all host cores (Eq. cost_2,
+    Eq. u_update); the GPU's x_next against the oracle's is reported."""
     prob = inp.stress_line()
     g = gpu_solve(M, prob)
-    K = prob["params"]["K"]
-    ks = np.unique(np.concatenate([np.arange(0, K, K // 96), [K - 1], np.argsort(g["costs"])[:32]]))
-    c_orc, gap = orc.sample_costs(prob, ks, n_threads=16)
-    err, grazing = cost_err(g["costs"][ks], c_orc, gap)
-    assert err <= COST_RTOL, (err, grazing)
-    S = g["costs"].astype(np.float64)
-    rc, w = orc.weights(S, prob["params"]["lambda"])
-    nz = np.nonzero(w > 1e-30)[0]
-    upd = np.zeros((prob["params"]["N"], 4))
-    for k in nz:
-        upd += w[k] * np.array([orc.noise(prob["params"], prob["iter"], int(k), j) for j in range(prob["params"]["N"])])
-    expect = prob["u_nom"].astype(np.float64) + upd
-    assert control_err(g["u_out"], expect, prob["params"]["sigma"]) <= U_RTOL
-    print("stress: sampled cost err", err, "grazing", grazing, "contributors", nz.size)
+    ref = orc.mppi_step(prob, n_threads=os.cpu_count() or 1)
+    e = assert_step_close(prob, g, ref)
+    print("stress errors", e, "ess", 1.0 / np.sum(ref["weights"] ** 2))
 
 
 def test_maximum_sizes(M, orc, inp):
-    """The ABI's limits, each at the largest value with the others small:
-    N = N_MAX steps and M = M_MAX obstacles against the full oracle step;
-    K = K_MAX samples with sampled costs and the update checked as
-    sum_k w_k delta_k (weights of the GPU's own costs in FP64, the oracle's
-    noise)."""
+    """The ABI's limits, each at the largest value with the others small,
+    against the full FP64 oracle step: N = N_MAX steps, M = M_MAX
+    obstacles, and K = K_MAX samples (every one of the 2^24 costs and the
+    update)."""
     prob = inp.eight_with_spheres(K=300, N=M.N_MAX, dt=0.002, M=16, t0=0.3, **{"lambda": 100.0})
     assert_step_close(prob, gpu_solve(M, prob), orc.mppi_step(prob, n_threads=16))
     prob = inp.eight_with_spheres(K=256, N=8, M=M.M_MAX, t0=0.3, **{"lambda": 100.0})
     g = gpu_solve(M, prob)
     assert g["status"] == M.OK
     assert_step_close(prob, g, orc.mppi_step(prob, n_threads=16))
-    # A low temperature keeps the contributors few enough to sum here.
-    prob = inp.plain_hover(K=M.K_MAX, N=1, seed=3, **{"lambda": 0.005})
+    prob = inp.plain_hover(K=M.K_MAX, N=1, seed=3)
     g = gpu_solve(M, prob)
-    K = prob["params"]["K"]
-    ks = np.unique(np.concatenate([np.arange(0, K, K // 64), [K - 1], np.argsort(g["costs"])[:16]]))
-    c_orc, gap = orc.sample_costs(prob, ks, n_threads=16)
-    err, _ = cost_err(g["costs"][ks], c_orc, gap)
-    assert err <= COST_RTOL, err
-    rc, w = orc.weights(g["costs"].astype(np.float64), prob["params"]["lambda"])
-    nz = np.nonzero(w > 1e-30)[0]
-    assert 0 < nz.size < 200000, nz.size
-    upd = np.zeros((1, 4))
-    for k in nz:
-        upd += w[k] * orc.noise(prob["params"], prob["iter"], int(k), 0)
-    assert control_err(g["u_out"], prob["u_nom"].astype(np.float64) + upd, prob["params"]["sigma"]) <= U_RTOL
-    print("K_MAX: contributors", nz.size)
+    ref = orc.mppi_step(prob, n_threads=os.cpu_count() or 1)
+    e = assert_step_close(prob, g, ref)
+    print("K_MAX errors", e, "ess", 1.0 / np.sum(ref["weights"] ** 2))
 
 
 def test_grid_collision_module(M, orc, inp):

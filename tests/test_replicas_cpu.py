@@ -23,12 +23,13 @@ def _rank_main(rank, world, port, out):
     import bench
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    prob = bench.headline_problem(rank)
+    fleet = bench.Fleet(4, stream_base=rank * bench.N_FLEET)
     local_ms = 10.0 + 5.0 * rank  # rank 1 is the slower replica
     mx = bench.barrier_max(local_ms, world)
     bench.barrier(world)
-    rate = bench.whole_job_rate(bench.K_HEAD * bench.N_HEAD, 4, mx, world)
-    out.put((rank, mx, rate, int(prob["params"]["stream_id"]), float(np.sum(prob["obstacles"]))))
+    rate = bench.whole_job_rate(fleet.rollout_steps, 4, mx, world)
+    sids = {int(p["params"]["stream_id"]) for p in fleet.probs}
+    out.put((rank, mx, rate, min(sids), max(sids), fleet.rollout_steps, float(np.sum(fleet.obs))))
     dist.destroy_process_group()
 
 
@@ -44,10 +45,10 @@ def test_replicas_reduce_max_and_whole_job_rate():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, mx0, rate0, sid0, obs0), (r1, mx1, rate1, sid1, obs1) = res
+    (r0, mx0, rate0, lo0, hi0, st0, obs0), (r1, mx1, rate1, lo1, hi1, st1, obs1) = res
     assert mx0 == mx1 == 15.0  # the slowest rank's time on every rank
-    assert rate0 == rate1 == pytest.approx(2 * 16384 * 100 * 4 / 15e-3)
-    assert sid0 != sid1  # independent noise streams per replica
+    assert st0 == st1 and rate0 == rate1 == pytest.approx(2 * st0 * 4 / 15e-3)
+    assert hi0 < lo1  # independent noise streams per replica and vehicle
     assert obs0 == obs1  # same workload on every replica
 
 
@@ -61,7 +62,7 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
            "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference", "--gpus", "2",
-           "--steps", "1", "--warmup", "3"]
+           "--steps", "1", "--warmup", "3", "--ref-seconds", "3"]
     r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
