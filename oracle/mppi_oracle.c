@@ -449,26 +449,34 @@ int orc_grid_occupied(const orc_params* P, const double p[3], double* face_gap)
 
 /* Obstacle cost of one state (Sec. IV-D): c_obs * 1[x in C_obs] (one
  * indicator per state), plus the exponential barrier of the reading
- * c_bar * exp(-beta * max(gap, 0)) summed over obstacles.  *min_gap gets
- * the smallest gap seen (used by tests to flag grazing samples). */
+ * c_bar * exp(-beta * max(gap, 0)) summed over obstacles.
+ * *min_gap (test instrumentation, not part of the cost) gets the smaller of
+ * itself and this state's distance from the indicator's discontinuity: the
+ * indicator flips where the state's smallest gap over the obstacles
+ * crosses 0, so that distance is |smallest gap| (and, with a grid, the
+ * distance to the nearest voxel face across which occupancy changes).
+ * Tests use it to flag samples with a state on a collision boundary. */
 double orc_obstacle_cost(const orc_params* P, const double x[13], const double* obs, int M,
                          double* min_gap)
 {
     double barrier = 0.0;
     int in_collision = 0;
+    double smallest = INFINITY;
     for (int o = 0; o < M; ++o) {
         double s = orc_obstacle_gap(P, x, &obs[4 * o]);
-        if (min_gap && s < *min_gap) *min_gap = s;
+        if (s < smallest) smallest = s;
         barrier += P->c_bar * exp(-P->beta * (s > 0.0 ? s : 0.0));
         if (s <= 0.0) in_collision = 1;
     }
+    double edge = fabs(smallest);
     if (P->grid) {
         double face = INFINITY;
         if (orc_grid_occupied(P, x, &face)) in_collision = 1;
         /* A position within `face` of an occupancy boundary: reported in
          * metres (the same grazing threshold applies). */
-        if (min_gap && face < *min_gap) *min_gap = face;
+        if (face < edge) edge = face;
     }
+    if (min_gap && edge < *min_gap) *min_gap = edge;
     return barrier + (in_collision ? P->c_obs : 0.0);
 }
 
@@ -560,7 +568,8 @@ void orc_shift(const orc_params* P, const double* u, const double u_init[4], dou
  *   u_next (N x 4)  warm start for the next iteration (shift / Sec. IV-B);
  *   x_next (13)     x_hat advanced by the applied command over the
  *                   control period alpha*dt (simulated plant, reading);
- *   costs  (K)      S_k; weights (K) w_k; min_gap (K) smallest obstacle gap.
+ *   costs  (K)      S_k; weights (K) w_k; min_gap (K) smallest distance of a
+ *                   state's collision test from its boundary (test flag).
  * Any output pointer may be NULL.  Delay compensation (Sec. IV-E): with
  * delay > 0 the rollouts start from x_hat predicted forward by `delay`
  * seconds under the feasible input of u_nom_0.

@@ -74,16 +74,18 @@ DevModel make_dev_model(const mppi_model& m) {
     const double a = (double)m.arm_l / std::sqrt(2.0), c = m.c_tf;
     d.a = (float)a;
     d.c_tf = m.c_tf;
-    // The allocation matrix of Sec. III-B has mutually orthogonal rows, so
-    // Gamma^-1 = Gamma^T diag(1/|row_i|^2).
-    const double G[4][4] = {{1, 1, 1, 1}, {-a, a, a, -a}, {-a, a, -a, a}, {-c, -c, c, c}};
-    const double n2[4] = {4.0, 4.0 * a * a, 4.0 * a * a, 4.0 * c * c};
-    for (int r = 0; r < 4; ++r)
-        for (int col = 0; col < 4; ++col) d.Ginv[4 * r + col] = (float)(G[col][r] / n2[col]);
     d.T_min = m.T_min; d.T_max = m.T_max; d.motor_clip = m.motor_clip;
     d.F_min = m.F_min; d.F_max = m.F_max;
     for (int i = 0; i < 3; ++i) d.w_max[i] = m.w_max[i];
     d.u_init[0] = (float)((double)m.mass * m.g);
+    // The allocation matrix of Sec. III-B, rows (1,1,1,1), a(-1,1,1,-1),
+    // a(-1,1,-1,1), c(-1,-1,1,1), has mutually orthogonal rows, so
+    // Gamma^-1 = Gamma^T diag(1/|row_i|^2): entries 1/4, +-1/(4a), +-1/(4c).
+    d.q_a = (float)(1.0 / (4.0 * a));
+    d.q_c = (float)(1.0 / (4.0 * c));
+    d.a_Jx = (float)(a / J[0]);
+    d.a_Jy = (float)(a / J[1]);
+    d.c_Jz = (float)(c / J[2]);
     return d;
 }
 

@@ -24,12 +24,17 @@ struct DevModel {
     float dJx, dJy, dJz;    // (Jz-Jy), (Jx-Jz), (Jy-Jx): omega x J omega terms
     float kx, ky, kz;       // dJ / J: gyroscopic angular-acceleration factors
     float a, c_tf;          // a = l / sqrt(2): entries of the allocation matrix
-    float Ginv[16];         // inverse allocation matrix, row major
     float T_min, T_max;
     int motor_clip;
     float F_min, F_max;
     float w_max[3];
     float u_init[4];        // hover: m g, 0, 0, 0
+    // Motor allocation in factored form (Gamma's rows are (1,1,1,1),
+    // a(-1,1,1,-1), a(-1,1,-1,1), c(-1,-1,1,1)): rotor thrusts from
+    // F/4 and the torques times q_a = 1/(4a), q_c = 1/(4c); torque over
+    // inertia from the clipped thrusts' differences times a/J_x, a/J_y, c/J_z.
+    float q_a, q_c;
+    float a_Jx, a_Jy, c_Jz;
 };
 
 // Cost weights and step options shared by every instance of a launch.

@@ -39,6 +39,8 @@ namespace mppi {
 // memory as five (round 2i, round 2i + 1) pairs.
 constexpr unsigned kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
 
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 __device__ __forceinline__ uint4 philox_round(uint4 c, unsigned k0, unsigned k1) {
     const unsigned hi0 = __umulhi(0xD2511F53u, c.x);
     const unsigned lo0 = 0xD2511F53u * c.x;
@@ -67,10 +69,8 @@ __device__ __forceinline__ float uniform01(unsigned r) {
     return __uint2float_rn(((r >> 9) << 1) | 1u) * 5.9604644775390625e-08f;
 }
 
-// Four standard normals for sample k, step j: Box-Muller on the two
-// uniform pairs of one Philox call.  Counter (k, j, iter), round keys rk.
-__device__ __forceinline__ float4 normals4(unsigned k, unsigned j, unsigned long long iter, const uint4* rk) {
-    const uint4 r = philox4x32_10(make_uint4(k, j, (unsigned)iter, (unsigned)(iter >> 32)), rk);
+// Box-Muller on the two uniform pairs of one Philox output.
+__device__ __forceinline__ float4 box_muller4(const uint4 r) {
     const float u0 = uniform01(r.x), u1 = uniform01(r.y), u2 = uniform01(r.z), u3 = uniform01(r.w);
     // -2 ln u > 0 for every u of the map (u < 1), so sqrt(x) = x rsqrt(x).
     const float a01 = -2.0f * logf(u0), a23 = -2.0f * logf(u2);
@@ -86,11 +86,58 @@ __device__ __forceinline__ float4 normals4(unsigned k, unsigned j, unsigned long
     return make_float4(-rad01 * c1, -rad01 * s1, -rad23 * c3, -rad23 * s3);
 }
 
+// Four standard normals for sample k, step j: Box-Muller on the two
+// uniform pairs of one Philox call.  Counter (k, j, iter), round keys rk.
+__device__ __forceinline__ float4 normals4(unsigned k, unsigned j, unsigned long long iter, const uint4* rk) {
+    return box_muller4(philox4x32_10(make_uint4(k, j, (unsigned)iter, (unsigned)(iter >> 32)), rk));
+}
+
+// The first round's output words that do not depend on the step j: two
+// that depend on the sample k only (and the counter's high word), two on
+// the tile's counter word only.  normals4_pre gives bitwise normals4.
+struct PhiloxPre {
+    unsigned z, w;  // per sample: mulhi(M0, k) ^ iter_hi ^ key1, M0 k
+};
+
+__device__ __forceinline__ PhiloxPre philox_pre_sample(unsigned k, unsigned long long iter, const uint4* rk) {
+    PhiloxPre p;
+    p.z = __umulhi(0xD2511F53u, k) ^ (unsigned)(iter >> 32) ^ rk[0].y;
+    p.w = 0xD2511F53u * k;
+    return p;
+}
+
+// Per tile: (mulhi(M1, iter_lo) ^ key0, M1 iter_lo).
+__device__ __forceinline__ uint2 philox_pre_tile(unsigned long long iter, const uint4* rk) {
+    const unsigned lo = (unsigned)iter;
+    return make_uint2(__umulhi(0xCD9E8D57u, lo) ^ rk[0].x, 0xCD9E8D57u * lo);
+}
+
+__device__ __forceinline__ float4 normals4_pre(unsigned j, const PhiloxPre p, const uint2* pt, const uint4* rk) {
+    const uint2 t = *pt;
+    uint4 c = make_uint4(t.x ^ j, t.y, p.z, p.w);
+    c = philox_round(c, rk[0].z, rk[0].w);
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        const uint4 k = rk[i];
+        c = philox_round(c, k.x, k.y);
+        c = philox_round(c, k.z, k.w);
+    }
+    return box_muller4(c);
+}
+
 // delta = sigma o z, rounded once (no contraction) so that the rollout and
 // the regeneration in the weighted sum see the same value.
 __device__ __forceinline__ float4 noise_delta(const float4 z, const float* sigma) {
-    return make_float4(__fmul_rn(sigma[0], z.x), __fmul_rn(sigma[1], z.y), __fmul_rn(sigma[2], z.z),
-                       __fmul_rn(sigma[3], z.w));
+    const float2 a = __fmul2_rn(f2(sigma[0], sigma[1]), f2(z.x, z.y));
+    const float2 b = __fmul2_rn(f2(sigma[2], sigma[3]), f2(z.z, z.w));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// u_nom_j + delta, rounded once per component (no contraction).
+__device__ __forceinline__ float4 perturb(const float4 un, const float4 d) {
+    const float2 a = __fadd2_rn(f2(un.x, un.y), f2(d.x, d.y));
+    const float2 b = __fadd2_rn(f2(un.z, un.w), f2(d.z, d.w));
+    return make_float4(a.x, a.y, b.x, b.y);
 }
 
 // ------------------------------------------------------------------ model
@@ -98,6 +145,27 @@ __device__ __forceinline__ float4 noise_delta(const float4 z, const float* sigma
 struct State {
     float px, py, pz, qw, qx, qy, qz, vx, vy, vz, wx, wy, wz;
 };
+
+// Packed FP32x2 arithmetic (two lanes' worth of work per instruction, each
+// element rounded exactly as the scalar operation).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// Compensated addition of inc to (x0, x1) with compensation terms (c0, c1).
+__device__ __forceinline__ void comp_add2(float& x0, float& x1, float& c0, float& c1, float i0, float i1) {
+    const float2 y = sub2(f2(i0, i1), f2(c0, c1));
+    const float2 x = f2(x0, x1);
+    const float2 t = __fadd2_rn(x, y);
+    const float2 c = sub2(sub2(t, x), y);
+    x0 = t.x; x1 = t.y;
+    c0 = c.x; c1 = c.y;
+}
 
 // Eq. drone_dynamics with collective thrust over mass Fm and torque over
 // inertia (tJx, tJy, tJz) held constant over the step.
@@ -111,9 +179,11 @@ __device__ __forceinline__ void deriv(const DevModel& M, const State& s, float F
     d.qx = s.qw * hx + s.qy * hz - s.qz * hy;
     d.qy = s.qw * hy - s.qx * hz + s.qz * hx;
     d.qz = s.qw * hz + s.qx * hy - s.qy * hx;
-    d.vx = 2.0f * (s.qx * s.qz + s.qw * s.qy) * Fm;
-    d.vy = 2.0f * (s.qy * s.qz - s.qw * s.qx) * Fm;
-    d.vz = (1.0f - 2.0f * (s.qx * s.qx + s.qy * s.qy)) * Fm - M.g;
+    // Thrust along the body z axis, R(q) e_z (F/m), then gravity.
+    const float F2 = 2.0f * Fm;
+    d.vx = (s.qx * s.qz + s.qw * s.qy) * F2;
+    d.vy = (s.qy * s.qz - s.qw * s.qx) * F2;
+    d.vz = fmaf(-F2, s.qx * s.qx + s.qy * s.qy, Fm - M.g);
     d.wx = tJx - M.kx * s.wy * s.wz;
     d.wy = tJy - M.ky * s.wz * s.wx;
     d.wz = tJz - M.kz * s.wx * s.wy;
@@ -150,31 +220,69 @@ __device__ __forceinline__ void axpy_inc(State& o, float h, const State& k) {
 // Classical RK4 step of length h, inputs held, then q renormalised.  The
 // four stage increments are summed first and added to the state once;
 // position and velocity carry a compensation term across steps so that
-// their FP32 rounding does not accumulate over the horizon.
+// their FP32 rounding does not accumulate over the horizon.  Since p_dot = v
+// and v_dot does not depend on p or v, the position increment of the four
+// stages is h v_0 + h^2/6 (a_1 + a_2 + a_3), a_i the stages' accelerations
+// (the classical combination written out), so the stages' velocities are
+// not formed.
 __device__ __forceinline__ void rk4(const DevModel& M, State& x, Comp& c, float Fm, float tJx, float tJy, float tJz,
                                     float h) {
-    const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
+    const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f), hh6 = h * h6;
     State k, xs, inc;
     deriv(M, x, Fm, tJx, tJy, tJz, k);
-    inc.px = h6 * k.px; inc.py = h6 * k.py; inc.pz = h6 * k.pz;
-    inc.qw = h6 * k.qw; inc.qx = h6 * k.qx; inc.qy = h6 * k.qy; inc.qz = h6 * k.qz;
-    inc.vx = h6 * k.vx; inc.vy = h6 * k.vy; inc.vz = h6 * k.vz;
-    inc.wx = h6 * k.wx; inc.wy = h6 * k.wy; inc.wz = h6 * k.wz;
-    axpy(xs, x, h2, k);
+    float ax = k.vx, ay = k.vy, az = k.vz;
+    // Attitude, rates and velocity increments in pairs (packed FP32x2).
+    float2 i_q0 = __fmul2_rn(f2(h6, h6), f2(k.qw, k.qx)), i_q1 = __fmul2_rn(f2(h6, h6), f2(k.qy, k.qz));
+    float2 i_w = __fmul2_rn(f2(h6, h6), f2(k.wx, k.wy)), i_v = __fmul2_rn(f2(h6, h6), f2(k.vx, k.vy));
+    float i_wz = h6 * k.wz, i_vz = h6 * k.vz;
+    const float2 x_q0 = f2(x.qw, x.qx), x_q1 = f2(x.qy, x.qz), x_w = f2(x.wx, x.wy);
+    auto stage = [&](float hs) {  // xs = x + hs k (attitude and rates; the rest is not used)
+        const float2 H = f2(hs, hs);
+        const float2 q0 = __ffma2_rn(H, f2(k.qw, k.qx), x_q0), q1 = __ffma2_rn(H, f2(k.qy, k.qz), x_q1);
+        const float2 w = __ffma2_rn(H, f2(k.wx, k.wy), x_w);
+        xs.qw = q0.x; xs.qx = q0.y; xs.qy = q1.x; xs.qz = q1.y;
+        xs.wx = w.x; xs.wy = w.y; xs.wz = fmaf(hs, k.wz, x.wz);
+        xs.vx = x.vx; xs.vy = x.vy; xs.vz = x.vz;
+        xs.px = x.px; xs.py = x.py; xs.pz = x.pz;
+    };
+    auto add = [&](float hc) {
+        const float2 H = f2(hc, hc);
+        i_q0 = __ffma2_rn(H, f2(k.qw, k.qx), i_q0);
+        i_q1 = __ffma2_rn(H, f2(k.qy, k.qz), i_q1);
+        i_w = __ffma2_rn(H, f2(k.wx, k.wy), i_w);
+        i_v = __ffma2_rn(H, f2(k.vx, k.vy), i_v);
+        i_wz = fmaf(hc, k.wz, i_wz);
+        i_vz = fmaf(hc, k.vz, i_vz);
+    };
+    stage(h2);
     deriv(M, xs, Fm, tJx, tJy, tJz, k);
-    axpy_inc(inc, h3, k);
-    axpy(xs, x, h2, k);
+    add(h3);
+    ax += k.vx; ay += k.vy; az += k.vz;
+    stage(h2);
     deriv(M, xs, Fm, tJx, tJy, tJz, k);
-    axpy_inc(inc, h3, k);
-    axpy(xs, x, h, k);
+    add(h3);
+    ax += k.vx; ay += k.vy; az += k.vz;
+    stage(h);
     deriv(M, xs, Fm, tJx, tJy, tJz, k);
-    axpy_inc(inc, h6, k);
-    comp_add(x.px, c.px, inc.px); comp_add(x.py, c.py, inc.py); comp_add(x.pz, c.pz, inc.pz);
-    comp_add(x.vx, c.vx, inc.vx); comp_add(x.vy, c.vy, inc.vy); comp_add(x.vz, c.vz, inc.vz);
-    x.qw += inc.qw; x.qx += inc.qx; x.qy += inc.qy; x.qz += inc.qz;
-    x.wx += inc.wx; x.wy += inc.wy; x.wz += inc.wz;
-    const float n = rsqrtf(x.qw * x.qw + x.qx * x.qx + x.qy * x.qy + x.qz * x.qz);
-    x.qw *= n; x.qx *= n; x.qy *= n; x.qz *= n;
+    add(h6);
+    inc.qw = i_q0.x; inc.qx = i_q0.y; inc.qy = i_q1.x; inc.qz = i_q1.y;
+    inc.wx = i_w.x; inc.wy = i_w.y; inc.wz = i_wz;
+    inc.vx = i_v.x; inc.vy = i_v.y; inc.vz = i_vz;
+    inc.px = fmaf(h, x.vx, hh6 * ax);
+    inc.py = fmaf(h, x.vy, hh6 * ay);
+    inc.pz = fmaf(h, x.vz, hh6 * az);
+    comp_add2(x.px, x.py, c.px, c.py, inc.px, inc.py);
+    comp_add2(x.vx, x.vy, c.vx, c.vy, inc.vx, inc.vy);
+    comp_add2(x.pz, x.vz, c.pz, c.vz, inc.pz, inc.vz);
+    float2 q0 = __fadd2_rn(f2(x.qw, x.qx), f2(inc.qw, inc.qx));
+    float2 q1 = __fadd2_rn(f2(x.qy, x.qz), f2(inc.qy, inc.qz));
+    const float2 w = __fadd2_rn(f2(x.wx, x.wy), f2(inc.wx, inc.wy));
+    x.wx = w.x; x.wy = w.y; x.wz += inc.wz;
+    const float2 n2 = __ffma2_rn(q1, q1, __fmul2_rn(q0, q0));
+    const float n = rsqrtf(n2.x + n2.y);
+    q0 = __fmul2_rn(q0, f2(n, n));
+    q1 = __fmul2_rn(q1, f2(n, n));
+    x.qw = q0.x; x.qx = q0.y; x.qy = q1.x; x.qz = q1.y;
 }
 
 // Uncompensated step (single use: prediction, plant step).
@@ -192,38 +300,50 @@ __device__ __forceinline__ float4 clamp_input(const DevModel& M, float4 u) {
 }
 
 struct Feasible {
-    float F, tx, ty, tz;    // clipped collective thrust and torques
-    float gx, gy, gz;       // omega x J omega at the step's start
+    float F, tx, ty, tz;     // clipped collective thrust and torques
+    float gx, gy, gz;        // omega x J omega at the step's start
+    float Fm, tJx, tJy, tJz; // F / m and the torques over the inertia (what the dynamics use)
 };
 
 // Constraint pipeline of Sec. III-B: desired rate change over dt ->
-// desired torque -> rotor thrusts (Gamma^-1) -> clip -> Gamma.
+// desired torque -> rotor thrusts (Gamma^-1) -> clip -> Gamma.  Gamma's
+// rows are orthogonal with entries +-1, +-a, +-c, so Gamma^-1 applies as
+// T_i = F/4 +- tau_x/(4a) +- tau_y/(4a) +- tau_z/(4c) and Gamma as sums and
+// differences of the clipped thrusts.
 __device__ __forceinline__ Feasible feasible(const DevModel& M, const State& s, float4 u, float inv_dt) {
     Feasible o;
     o.gx = M.dJx * s.wy * s.wz;
     o.gy = M.dJy * s.wz * s.wx;
     o.gz = M.dJz * s.wx * s.wy;
-    float F = u.x;
-    float tx = fmaf(M.Jx, (u.y - s.wx) * inv_dt, o.gx);
-    float ty = fmaf(M.Jy, (u.z - s.wy) * inv_dt, o.gy);
-    float tz = fmaf(M.Jz, (u.w - s.wz) * inv_dt, o.gz);
+    const float rx = (u.y - s.wx) * inv_dt, ry = (u.z - s.wy) * inv_dt, rz = (u.w - s.wz) * inv_dt;
     if (M.motor_clip) {
-        float T[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float t = M.Ginv[4 * r + 0] * F + M.Ginv[4 * r + 1] * tx + M.Ginv[4 * r + 2] * ty +
-                            M.Ginv[4 * r + 3] * tz;
-            T[r] = fminf(fmaxf(t, M.T_min), M.T_max);
-        }
-        F = (T[0] + T[1]) + (T[2] + T[3]);
-        tx = M.a * ((T[1] + T[2]) - (T[0] + T[3]));
-        ty = M.a * ((T[1] + T[3]) - (T[0] + T[2]));
-        tz = M.c_tf * ((T[2] + T[3]) - (T[0] + T[1]));
+        const float tx = fmaf(M.Jx, rx, o.gx), ty = fmaf(M.Jy, ry, o.gy), tz = fmaf(M.Jz, rz, o.gz);
+        const float f0 = 0.25f * u.x, ex = tx * M.q_a, ey = ty * M.q_a, ez = tz * M.q_c;
+        const float A = f0 - ez, B = f0 + ez, P = ex + ey, Q = ex - ey;
+        const float T0 = fminf(fmaxf(A - P, M.T_min), M.T_max);
+        const float T1 = fminf(fmaxf(A + P, M.T_min), M.T_max);
+        const float T2 = fminf(fmaxf(B + Q, M.T_min), M.T_max);
+        const float T3 = fminf(fmaxf(B - Q, M.T_min), M.T_max);
+        const float s01 = T0 + T1, s23 = T2 + T3;
+        const float dx = (T1 + T2) - (T0 + T3), dy = (T1 + T3) - (T0 + T2), dz = s23 - s01;
+        o.F = s01 + s23;
+        o.tx = M.a * dx;
+        o.ty = M.a * dy;
+        o.tz = M.c_tf * dz;
+        o.Fm = o.F * M.inv_mass;
+        o.tJx = M.a_Jx * dx;
+        o.tJy = M.a_Jy * dy;
+        o.tJz = M.c_Jz * dz;
+    } else {
+        o.F = u.x;
+        o.tx = fmaf(M.Jx, rx, o.gx);
+        o.ty = fmaf(M.Jy, ry, o.gy);
+        o.tz = fmaf(M.Jz, rz, o.gz);
+        o.Fm = u.x * M.inv_mass;
+        o.tJx = fmaf(M.kx, s.wy * s.wz, rx);
+        o.tJy = fmaf(M.ky, s.wz * s.wx, ry);
+        o.tJz = fmaf(M.kz, s.wx * s.wy, rz);
     }
-    o.F = F;
-    o.tx = tx;
-    o.ty = ty;
-    o.tz = tz;
     return o;
 }
 
@@ -232,31 +352,41 @@ __device__ __forceinline__ Feasible feasible(const DevModel& M, const State& s, 
 // Input and input-change cost of one step (Eq. cost): ||u_j||^2_R and, from
 // the second step on, ||u_j - u_{j-1}||^2_{R_Delta}.
 __device__ __forceinline__ float input_cost(const DevCost& C, const float4 u, const float4 u_prev, bool rate) {
-    float c = fmaf(C.R[0], u.x * u.x, fmaf(C.R[1], u.y * u.y, fmaf(C.R[2], u.z * u.z, C.R[3] * u.w * u.w)));
+    const float2 a = f2(u.x, u.y), b = f2(u.z, u.w);
+    const float2 t = __ffma2_rn(f2(C.R[2], C.R[3]), __fmul2_rn(b, b), __fmul2_rn(f2(C.R[0], C.R[1]), __fmul2_rn(a, a)));
+    float c = t.x + t.y;
     if (rate) {
-        const float ex = u.x - u_prev.x, ey = u.y - u_prev.y, ez = u.z - u_prev.z, ew = u.w - u_prev.w;
-        c += fmaf(C.Rd[0], ex * ex, fmaf(C.Rd[1], ey * ey, fmaf(C.Rd[2], ez * ez, C.Rd[3] * ew * ew)));
+        const float2 ea = sub2(a, f2(u_prev.x, u_prev.y)), eb = sub2(b, f2(u_prev.z, u_prev.w));
+        const float2 r = __ffma2_rn(f2(C.Rd[2], C.Rd[3]), __fmul2_rn(eb, eb),
+                                    __fmul2_rn(f2(C.Rd[0], C.Rd[1]), __fmul2_rn(ea, ea)));
+        c += r.x + r.y;
     }
     return c;
 }
 
-// rho_ref of Sec. IV-C against one padded reference row (16 floats).
-// The compensation terms c hold minus the low-order parts of p and v.
+// rho_ref of Sec. IV-C against one reference row staged as four float4:
+// (px, py, vx, vy), (pz, vz, wx, wy), (qw, qx, qy, qz), (wz, -, -, -), so
+// that the differences pair up for packed arithmetic.  The compensation
+// terms c hold minus the low-order parts of p and v.
 __device__ __forceinline__ float tracking_cost(const DevCost& C, const State& x, const Comp& c, const float4* row) {
     const float4 r0 = row[0], r1 = row[1], r2 = row[2], r3 = row[3];
-    const float dpx = (x.px - r0.x) - c.px, dpy = (x.py - r0.y) - c.py, dpz = (x.pz - r0.z) - c.pz;
-    const float dvx = (x.vx - r1.w) - c.vx, dvy = (x.vy - r2.x) - c.vy, dvz = (x.vz - r2.y) - c.vz;
-    const float dwx = x.wx - r2.z, dwy = x.wy - r2.w, dwz = x.wz - r3.x;
-    const float dot = x.qw * r0.w + x.qx * r1.x + x.qy * r1.y + x.qz * r1.z;
+    const float2 dp = sub2(sub2(f2(x.px, x.py), f2(r0.x, r0.y)), f2(c.px, c.py));
+    const float2 dv = sub2(sub2(f2(x.vx, x.vy), f2(r0.z, r0.w)), f2(c.vx, c.vy));
+    const float2 dz = sub2(sub2(f2(x.pz, x.vz), f2(r1.x, r1.y)), f2(c.pz, c.vz));  // (p_z, v_z)
+    const float2 dw = sub2(f2(x.wx, x.wy), f2(r1.z, r1.w));
+    const float dwz = x.wz - r3.x;
+    const float2 qd = __ffma2_rn(f2(x.qy, x.qz), f2(r2.z, r2.w), __fmul2_rn(f2(x.qw, x.qx), f2(r2.x, r2.y)));
+    const float dot = qd.x + qd.y;
     float d;
     if (C.quat_metric == 0) {
         d = 1.0f - dot * dot;
     } else {
         d = acosf(fminf(fmaxf(2.0f * dot * dot - 1.0f, -1.0f), 1.0f));
     }
-    const float ep = fmaf(dpx, dpx, fmaf(dpy, dpy, dpz * dpz));
-    const float ev = fmaf(dvx, dvx, fmaf(dvy, dvy, dvz * dvz));
-    const float ew = fmaf(dwx, dwx, fmaf(dwy, dwy, dwz * dwz));
+    const float2 sp = __fmul2_rn(dp, dp), sv = __fmul2_rn(dv, dv), sz = __fmul2_rn(dz, dz), sw = __fmul2_rn(dw, dw);
+    const float ep = (sp.x + sp.y) + sz.x;
+    const float ev = (sv.x + sv.y) + sz.y;
+    const float ew = fmaf(dwz, dwz, sw.x + sw.y);
     return fmaf(C.c_p, ep, fmaf(C.c_q, d * d, fmaf(C.c_v, ev, C.c_w * ew)));
 }
 
@@ -282,16 +412,10 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 // built), so it is reused while all of the warp's positions stay inside.
 // Replicated in every lane.  n = -1: no list yet; -2: a list did not fit
 // (more than 64 kept), lists are not used for the rest of the rollout.
-// np >= n: the list's length after padding (see obstacle_cost).
 struct WarpList {
     float lx, ly, lz, hx, hy, hz;
-    int n, np;
+    int n;
 };
-
-// Padding entry of a kept-obstacle list: its squared gap overflows to
-// +inf, so its term is below the floor (never added) and it is never in
-// collision.
-constexpr float kFarObstacle = 1.0e30f;
 
 // Obstacle term of Sec. IV-D at NP positions p[i] (origin-shifted) of the
 // lane's sample: bar_out[i] = the barrier sum c_bar sum_o exp(-beta
@@ -388,16 +512,6 @@ __device__ __forceinline__ void obstacle_cost_n(const DevCost& C, const float (&
                 for (int i = 0; i < NP; ++i) add(term(q, i), i);
             }
         };
-        // Fills list entries [cnt, padded) with far-away padding so that
-        // the scoring loop runs only whole groups of four independent terms
-        // (a leftover term runs alone, with the full latency of its chain).
-        auto pad = [&](int cnt) -> int {
-            const int padded = min((cnt + 4 * LANES - 1) / (4 * LANES) * (4 * LANES), 64);
-            for (int i = cnt + wlane; i < padded; i += 32)
-                wob[i] = make_float4(kFarObstacle, kFarObstacle, kFarObstacle, 0.0f);
-            __syncwarp();
-            return padded;
-        };
         bool have = false;
         if (reuse && wl.n >= 0) {
             bool in = true;
@@ -472,7 +586,7 @@ __device__ __forceinline__ void obstacle_cost_n(const DevCost& C, const float (&
                     base += cnt;
                 } else {
                     *kept_out += (unsigned)(NP * cnt);
-                    score(pad(cnt));
+                    score(cnt);
                     __syncwarp();
                 }
             }
@@ -480,13 +594,12 @@ __device__ __forceinline__ void obstacle_cost_n(const DevCost& C, const float (&
                 wl.lx = tlx; wl.ly = tly; wl.lz = tlz;
                 wl.hx = thx; wl.hy = thy; wl.hz = thz;
                 wl.n = base;
-                wl.np = pad(base);
                 have = true;
             }
         }
         if (have) {
             *kept_out += (unsigned)(NP * wl.n);
-            score(wl.np);
+            score(wl.n);
             __syncwarp();
         }
     }
@@ -673,6 +786,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
     __shared__ double s_redd[32];
     __shared__ float s_red[32];
     __shared__ uint4 s_rk[5];  // Philox round keys of the tile's instance
+    __shared__ uint2 s_pt;     // the first round's per-tile words
 
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
@@ -743,6 +857,10 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
         const float dt = sI.dt, inv_dt = 1.0f / sI.dt, lambda = sI.lambda;
         const unsigned long long iter = sI.iter_dev ? *sI.iter_dev : sI.iter;
         if (tid < 5) s_rk[tid] = philox_round_keys(sI.key0, sI.key1, (unsigned)tid);
+        if (tid == 0) {
+            const uint4 rk0 = philox_round_keys(sI.key0, sI.key1, 0u);
+            s_pt = philox_pre_tile(iter, &rk0);
+        }
         float sigma[4] = {sI.sigma[0], sI.sigma[1], sI.sigma[2], sI.sigma[3]};
 
         // ---------------------------------- stage inputs in shared memory
@@ -757,9 +875,9 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
         const float p0x = s_xhat[0], p0y = s_xhat[1], p0z = s_xhat[2];
         for (int j = tid; j <= N; j += nthreads) {
             const float* r = sI.ref + 13 * (size_t)j;
-            sref[4 * j + 0] = make_float4(r[0] - p0x, r[1] - p0y, r[2] - p0z, r[3]);
-            sref[4 * j + 1] = make_float4(r[4], r[5], r[6], r[7]);
-            sref[4 * j + 2] = make_float4(r[8], r[9], r[10], r[11]);
+            sref[4 * j + 0] = make_float4(r[0] - p0x, r[1] - p0y, r[7], r[8]);
+            sref[4 * j + 1] = make_float4(r[2] - p0z, r[9], r[10], r[11]);
+            sref[4 * j + 2] = make_float4(r[3], r[4], r[5], r[6]);
             sref[4 * j + 3] = make_float4(r[12], 0.0f, 0.0f, 0.0f);
         }
         for (int j = tid; j < N; j += nthreads) {
@@ -777,7 +895,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 const float* u = sI.u_nom;
                 const float4 u0 = clamp_input(Mdl, make_float4(u[0], u[1], u[2], u[3]));
                 const Feasible f = feasible(Mdl, x, u0, inv_dt);
-                rk4(Mdl, x, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, C.delay);
+                rk4(Mdl, x, f.Fm, f.tJx, f.tJy, f.tJz, C.delay);
             }
             s_x0[0] = x.px; s_x0[1] = x.py; s_x0[2] = x.pz; s_x0[3] = x.qw; s_x0[4] = x.qx;
             s_x0[5] = x.qy; s_x0[6] = x.qz; s_x0[7] = x.vx; s_x0[8] = x.vy; s_x0[9] = x.vz;
@@ -824,22 +942,21 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             unsigned kept = 0;  // obstacles evaluated by this warp (uniform over the warp)
             WarpList wl;
             wl.n = -1;
-            wl.np = 0;
             kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
                                  obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, wl, cull_margin,
                                                       reuse_lists, &hit, &kept));
             if (C.grid) hit |= grid_hit(C, x.px + p0x, x.py + p0y, x.pz + p0z);
             nhit += hit ? 1 : 0;
             float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+            const PhiloxPre ppre = philox_pre_sample(k, iter, s_rk);
             for (int j = 0; j < N; ++j) {
-                const float4 d = noise_delta(normals4(k, (unsigned)j, iter, s_rk), sigma);
+                const float4 d = noise_delta(normals4_pre((unsigned)j, ppre, &s_pt, s_rk), sigma);
                 const float4 un = su[j];
-                const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
-                                                              __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
+                const float4 u = clamp_input(Mdl, perturb(un, d));
                 float step = input_cost(C, u, u_prev, j > 0);
                 u_prev = u;
                 const Feasible f = feasible(Mdl, x, u, inv_dt);
-                rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
+                rk4(Mdl, x, cmp, f.Fm, f.tJx, f.tJy, f.tJz, dt);
                 step += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
                 step += obstacle_cost<LANES>(C, x.px - cmp.px, x.py - cmp.py, x.pz - cmp.pz, sobs, M, lane, wlane, wob,
                                              wl, cull_margin, reuse_lists, &hit, &kept);
@@ -888,18 +1005,18 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             x.wx = s_x0[10]; x.wy = s_x0[11]; x.wz = s_x0[12];
             Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (!is_cost) {
-                float4 d_next = noise_delta(normals4(k, 0u, iter, s_rk), sigma);
+                const PhiloxPre ppre = philox_pre_sample(k, iter, s_rk);
+                float4 d_next = noise_delta(normals4_pre(0u, ppre, &s_pt, s_rk), sigma);
                 for (int j = 0; j < N; ++j) {
                     const unsigned g = g_run + (unsigned)j;
                     const int slot = slot_of(g);
                     const unsigned ph = (g / kRing) & 1u;
                     const float4 d = d_next;
-                    d_next = noise_delta(normals4(k, (unsigned)min(j + 1, N - 1), iter, s_rk), sigma);
+                    d_next = noise_delta(normals4_pre((unsigned)min(j + 1, N - 1), ppre, &s_pt, s_rk), sigma);
                     const float4 un = su[j];
-                    const float4 u = clamp_input(Mdl, make_float4(__fadd_rn(un.x, d.x), __fadd_rn(un.y, d.y),
-                                                                  __fadd_rn(un.z, d.z), __fadd_rn(un.w, d.w)));
+                    const float4 u = clamp_input(Mdl, perturb(un, d));
                     const Feasible f = feasible(Mdl, x, u, inv_dt);
-                    rk4(Mdl, x, cmp, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz, dt);
+                    rk4(Mdl, x, cmp, f.Fm, f.tJx, f.tJy, f.tJz, dt);
                     // The tracking cost is formed here; the input and
                     // input-change cost by the cost lanes, from the control
                     // handed over with the position.
@@ -917,7 +1034,6 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 unsigned kept = 0;
                 WarpList wl;
                 wl.n = -1;
-                wl.np = 0;
                 kahan_add(S, Sc, tracking_cost(C, x, cmp, &sref[0]) +
                                      obstacle_cost<LANES>(C, x.px, x.py, x.pz, sobs, M, lane, wlane, wob, wl,
                                                           cull_margin, reuse_lists, &hit, &kept));
@@ -1219,7 +1335,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                     sI.u_cmd[3] = xh.wz + (f.tz - f.gz) * Mdl.inv_Jz * dt;
                 }
                 if (sI.x_next) {
-                    rk4(Mdl, xh, f.F * Mdl.inv_mass, f.tx * Mdl.inv_Jx, f.ty * Mdl.inv_Jy, f.tz * Mdl.inv_Jz,
+                    rk4(Mdl, xh, f.Fm, f.tJx, f.tJy, f.tJz,
                         C.shift_alpha * dt);
                     const float v[13] = {xh.px, xh.py, xh.pz, xh.qw, xh.qx, xh.qy, xh.qz,
                                          xh.vx, xh.vy, xh.vz, xh.wx, xh.wy, xh.wz};

@@ -5,9 +5,11 @@ Tolerances (FP32 kernel against the FP64 oracle on identical FP32 inputs):
 * control update u_out (and the warm start, the command): 1e-4 relative per
   control, measured against max(|u_oracle|, sigma_c) so that body-rate
   entries passing through zero are judged on the scale of their noise;
-* samples whose oracle trajectory grazes an obstacle boundary (smallest
-  squared gap within 1e-4 m^2) are left out of the cost comparison, because
-  the collision indicator is discontinuous there (their weight is ~0);
+* samples with a state whose collision test is within 1e-4 of its boundary
+  (the state's smallest squared gap over the obstacles within 1e-4 m^2 of
+  0, or its position within 1e-4 m of an occupancy-changing voxel face) are
+  left out of the cost comparison, because the once-per-state collision
+  indicator is discontinuous there; the update comparison keeps them;
 * the plant state x_next is the plant step of the applied command, which is
   formed from u_out_0 (R26): it is compared, 1e-4 relative per component
   (floor 1e-3), with the oracle's plant step of the GPU's own u_out_0, so

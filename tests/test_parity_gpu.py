@@ -93,7 +93,7 @@ def test_collisions_in_rollouts(M, orc, inp):
     obs[:, 1] += 0.7
     prob["obstacles"] = np.ascontiguousarray(obs)
     ref = orc.mppi_step(prob, n_threads=8)
-    assert np.mean(ref["min_gap"] <= 0) > 0.05
+    assert np.mean(ref["costs"] >= prob["params"]["c_obs"]) > 0.05  # many rollouts collide
     assert_step_close(prob, gpu_solve(M, prob), ref)
 
 
