@@ -417,6 +417,28 @@ struct WarpList {
     int n;
 };
 
+// A warp's kept-obstacle list in shared memory, in pairs: obstacles 2p and
+// 2p + 1 are the three float4 at 3p: (x0, x1, y0, y1), (z0, z1, w0, w1) with
+// w = 1 for a sphere and 0 for a vertical cylinder (whose z is 0 and does
+// not count), (rr0, rr1, -, -) the squared reach (radius + r_uav)^2.  Two
+// obstacles are scored with one set of packed FP32x2 instructions.  A list
+// of odd length ends with a far-away entry whose squared gap overflows to
+// +inf (its term is below the floor: never added; never in collision).
+constexpr int kListPairs = 32;          // 64 obstacles per warp
+constexpr int kListF4PerWarp = 3 * kListPairs;
+constexpr float kFarObstacle = 1.0e30f;
+
+__device__ __forceinline__ void list_put(float4* wob, int idx, const float4 ob) {
+    float* f = reinterpret_cast<float*>(wob + 3 * (idx >> 1));
+    const int e = idx & 1;
+    const bool sph = ob.w >= 0.0f;
+    f[e] = ob.x;
+    f[2 + e] = ob.y;
+    f[4 + e] = sph ? ob.z : 0.0f;
+    f[6 + e] = sph ? 1.0f : 0.0f;
+    f[8 + e] = fabsf(ob.w);
+}
+
 // Obstacle term of Sec. IV-D at NP positions p[i] (origin-shifted) of the
 // lane's sample: bar_out[i] = the barrier sum c_bar sum_o exp(-beta
 // max(gap_o, 0)), each term below its floor 2^-kBarrierFloorLog2 taken as 0,
@@ -436,81 +458,85 @@ struct WarpList {
 // `margin` and reused while the positions stay inside; obstacles kept only
 // by the margin add exactly +0, so the sum equals the uncut sum.
 // With LANES lanes per sample the lanes of a sample take every LANES-th
-// kept obstacle and combine by xor-shuffles (bitwise identical results on
-// all lanes of the sample).  `reuse` false (launches that count evaluated
-// pairs) culls every step.
+// pair of kept obstacles and combine by xor-shuffles (bitwise identical
+// results on all lanes of the sample).  `reuse` false (launches that count
+// evaluated pairs) culls every step.
 template <int LANES, int NP>
 __device__ __forceinline__ void obstacle_cost_n(const DevCost& C, const float (&px)[NP], const float (&py)[NP],
                                                 const float (&pz)[NP], const float4* so, int M, int lane, int wlane,
                                                 float4* wob, WarpList& wl, float margin, bool reuse,
                                                 float (&bar_out)[NP], bool (&hit_out)[NP], unsigned* kept_out) {
-    float bar[NP];
-    bool hit[NP];
+    float bar[NP], smin[NP];  // smin: smallest squared gap (the state is in collision iff <= 0)
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         bar[i] = 0.0f;
-        hit[i] = false;
+        smin[i] = INFINITY;
     }
     if (M > 0) {
-        // term: the exponent -beta log2(e) max(gap, 0) of one obstacle at
-        // position i; add: its barrier term, exactly 0 below the floor
-        // whichever box kept the obstacle, so the sum does not depend on the
-        // culling.
-        auto term = [&](const float4 ob, const int i) {
-            const float dx = px[i] - ob.x, dy = py[i] - ob.y, dz = pz[i] - ob.z;
-            const float sph = ob.w >= 0.0f ? dz : 0.0f;  // vertical cylinders ignore z
-            const float sg = fmaf(dx, dx, fmaf(dy, dy, sph * dz)) - fabsf(ob.w);
-            hit[i] |= (sg <= 0.0f);
-            return -C.beta_log2e * fmaxf(sg, 0.0f);
+        float2 PX[NP], PY[NP], PZ[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            PX[i] = f2(px[i], px[i]);
+            PY[i] = f2(py[i], py[i]);
+            PZ[i] = f2(pz[i], pz[i]);
+        }
+        const float2 NB = f2(-C.beta_log2e, -C.beta_log2e);
+        // term2: the exponents -beta log2(e) max(gap, 0) of the pair at list
+        // position 3q for position i; add: their barrier terms in list
+        // order, exactly 0 below the floor whichever box kept the obstacle,
+        // so the sum does not depend on the culling.
+        auto term2 = [&](const int q, const int i) {
+            const float4 A = wob[q], B = wob[q + 1], R = wob[q + 2];
+            const float2 dx = sub2(PX[i], f2(A.x, A.y)), dy = sub2(PY[i], f2(A.z, A.w));
+            const float2 dz = sub2(PZ[i], f2(B.x, B.y));
+            const float2 dzw = __fmul2_rn(dz, f2(B.z, B.w));
+            float2 sg = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+            sg = sub2(__ffma2_rn(dzw, dz, sg), f2(R.x, R.y));
+            smin[i] = fminf(smin[i], fminf(sg.x, sg.y));
+            return __fmul2_rn(NB, f2(fmaxf(sg.x, 0.0f), fmaxf(sg.y, 0.0f)));
         };
-        auto add = [&](const float a, const int i) {
-            if (a >= -kBarrierFloorLog2) bar[i] += ex2_ftz(a);
+        auto add = [&](const float2 a, const int i) {
+            if (a.x >= -kBarrierFloorLog2) bar[i] += ex2_ftz(a.x);
+            if (a.y >= -kBarrierFloorLog2) bar[i] += ex2_ftz(a.y);
         };
-        // Eight terms at a time (one position: eight obstacles, then four;
-        // two positions: four obstacles each): their loads and arithmetic
-        // are independent, only the additions stay in list order.
+        // Four pairs at a time (one position; two positions: two pairs
+        // each): their loads and arithmetic are independent, only the
+        // additions stay in list order.
         auto score = [&](int cnt) {
+            const int np = (cnt + 1) >> 1;
             int c = lane;
             if (NP == 1) {
-                for (; c + 7 * LANES < cnt; c += 8 * LANES) {
-                    const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
-                    const float4 q4 = wob[c + 4 * LANES], q5 = wob[c + 5 * LANES], q6 = wob[c + 6 * LANES],
-                                 q7 = wob[c + 7 * LANES];
-                    const float a0 = term(q0, 0), a1 = term(q1, 0), a2 = term(q2, 0), a3 = term(q3, 0);
-                    const float a4 = term(q4, 0), a5 = term(q5, 0), a6 = term(q6, 0), a7 = term(q7, 0);
+                for (; c + 3 * LANES < np; c += 4 * LANES) {
+                    const float2 a0 = term2(3 * c, 0), a1 = term2(3 * (c + LANES), 0);
+                    const float2 a2 = term2(3 * (c + 2 * LANES), 0), a3 = term2(3 * (c + 3 * LANES), 0);
                     add(a0, 0);
                     add(a1, 0);
                     add(a2, 0);
                     add(a3, 0);
-                    add(a4, 0);
-                    add(a5, 0);
-                    add(a6, 0);
-                    add(a7, 0);
                 }
             }
-            for (; c + 3 * LANES < cnt; c += 4 * LANES) {
-                const float4 q0 = wob[c], q1 = wob[c + LANES], q2 = wob[c + 2 * LANES], q3 = wob[c + 3 * LANES];
-                float a[NP][4];
+            for (; c + LANES < np; c += 2 * LANES) {
+                float2 a[NP][2];
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    a[i][0] = term(q0, i);
-                    a[i][1] = term(q1, i);
-                    a[i][2] = term(q2, i);
-                    a[i][3] = term(q3, i);
+                    a[i][0] = term2(3 * c, i);
+                    a[i][1] = term2(3 * (c + LANES), i);
                 }
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
                     add(a[i][0], i);
                     add(a[i][1], i);
-                    add(a[i][2], i);
-                    add(a[i][3], i);
                 }
             }
-            for (; c < cnt; c += LANES) {
-                const float4 q = wob[c];
+            for (; c < np; c += LANES) {
 #pragma unroll
-                for (int i = 0; i < NP; ++i) add(term(q, i), i);
+                for (int i = 0; i < NP; ++i) add(term2(3 * c, i), i);
             }
+        };
+        // Ends a list of odd length with the far-away entry.
+        auto seal = [&](int cnt) {
+            if ((cnt & 1) && wlane == 0) list_put(wob, cnt, make_float4(kFarObstacle, 0.0f, 0.0f, 0.0f));
+            __syncwarp();
         };
         bool have = false;
         if (reuse && wl.n >= 0) {
@@ -568,7 +594,7 @@ __device__ __forceinline__ void obstacle_cost_n(const DevCost& C, const float (&
                 const unsigned m1 = __ballot_sync(0xffffffffu, k1);
                 const int n0 = __popc(m0);
                 const int cnt = n0 + __popc(m1);
-                if (fits && base + cnt > 64) {
+                if (fits && base + cnt > 2 * kListPairs) {
                     // Too many for one list: score this step chunk by chunk
                     // with the warp's own box, and stop building lists.
                     fits = false;
@@ -579,13 +605,14 @@ __device__ __forceinline__ void obstacle_cost_n(const DevCost& C, const float (&
                     continue;
                 }
                 const int at = fits ? base : 0;
-                if (k0) wob[at + __popc(m0 & lt)] = ob0;
-                if (k1) wob[at + n0 + __popc(m1 & lt)] = ob1;
+                if (k0) list_put(wob, at + __popc(m0 & lt), ob0);
+                if (k1) list_put(wob, at + n0 + __popc(m1 & lt), ob1);
                 __syncwarp();
                 if (fits) {
                     base += cnt;
                 } else {
                     *kept_out += (unsigned)(NP * cnt);
+                    seal(cnt);
                     score(cnt);
                     __syncwarp();
                 }
@@ -594,6 +621,7 @@ __device__ __forceinline__ void obstacle_cost_n(const DevCost& C, const float (&
                 wl.lx = tlx; wl.ly = tly; wl.lz = tlz;
                 wl.hx = thx; wl.hy = thy; wl.hz = thz;
                 wl.n = base;
+                seal(base);
                 have = true;
             }
         }
@@ -605,16 +633,17 @@ __device__ __forceinline__ void obstacle_cost_n(const DevCost& C, const float (&
     }
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
+        bool hit = smin[i] <= 0.0f;
         if (LANES > 1) {
-            unsigned h = hit[i] ? 1u : 0u;
+            unsigned h = hit ? 1u : 0u;
 #pragma unroll
             for (int off = LANES / 2; off > 0; off >>= 1) {
                 bar[i] += __shfl_xor_sync(0xffffffffu, bar[i], off, LANES);
                 h |= __shfl_xor_sync(0xffffffffu, h, off, LANES);
             }
-            hit[i] = h != 0u;
+            hit = h != 0u;
         }
-        hit_out[i] = hit[i];
+        hit_out[i] = hit;
         bar_out[i] = C.c_bar * bar[i];
     }
 }
@@ -759,7 +788,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.e = o;    o = align_up(o + 4u * (unsigned)spb, 128);
     L.list = o; o = align_up(o + 4u * (unsigned)spb, 128);
     L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
-    L.wlist = o; o = align_up(o + 32u * (unsigned)block, 128);  // 64 float4 per warp
+    L.wlist = o; o = align_up(o + 48u * (unsigned)block, 128);  // 96 float4 (32 obstacle pairs) per warp
     L.xring = o; o = align_up(o + 16u * kSlotF4 * slots, 128);
     L.bars = o;  o = align_up(o + 8u * 4u * (slots / 32u), 128);
     L.total = o;
@@ -806,7 +835,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
     float* sE = reinterpret_cast<float*>(smem + L.e);
     int* slist = reinterpret_cast<int*>(smem + L.list);
     float4* spart = reinterpret_cast<float4*>(smem + L.part);
-    float4* wob = reinterpret_cast<float4*>(smem + L.wlist) + 64 * (threadIdx.x >> 5);
+    float4* wob = reinterpret_cast<float4*>(smem + L.wlist) + kListF4PerWarp * (threadIdx.x >> 5);
 
     const unsigned bar = smem_addr(&mbar);
     unsigned phase = 0;

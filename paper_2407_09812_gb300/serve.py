@@ -116,21 +116,26 @@ class Server:
             pass
 
 
-def run_fleet(duration_s: float = 5.0, n_vehicles: int = 1000, slots: int = 4, max_batch: int = 32,
-              warmup_s: float = 1.0, seed: int = 4, rate_hz: float = 100.0, queue_capacity: int = 0) -> dict:
+def run_fleet(duration_s: float = 5.0, n_vehicles: int = 1000, slots: int = 3, max_batch: int = 512,
+              max_batch_samples: int = 1 << 21, warmup_s: float = 1.0, seed: int = 4, rate_hz: float = 100.0,
+              queue_capacity: int = 0) -> dict:
     """Serves a fleet (K in {2048, 8192, 32768}, N in {50, 100}, 32 spheres
     each) for `duration_s` after `warmup_s`; reports solves/s,
-    rollout-steps/s and p50/p99 latency of the completed requests.  The
-    queue holds at most `queue_capacity` requests (0: two batches per
+    rollout-steps/s and p50/p99 latency of the completed requests.  A batch
+    takes whatever is queued when a slot frees, up to `max_batch_samples`
+    samples (and `max_batch` instances), so its size follows the queue
+    depth: small batches at light load, large ones at saturation.  The
+    queue holds at most `queue_capacity` requests (0: two full batches per
     slot); submissions beyond it are rejected (backpressure), which bounds
     the queueing delay when the offered load exceeds the GPU."""
-    queue_capacity = queue_capacity or 2 * slots * max_batch
     fleet = I.serving_fleet(n_vehicles=n_vehicles, seed=seed)
+    mean_K = float(np.mean([v["K"] for v in fleet]))
+    queue_capacity = queue_capacity or int(2 * slots * max(1, min(max_batch, max_batch_samples // mean_K)))
     model = I.model(motor_clip=1)
     params = I.params()
     srv = Server(model, params, {"max_vehicles": n_vehicles, "slots": slots, "max_batch": max_batch,
                                  "N_max": 100, "M_max": 32, "queue_capacity": queue_capacity,
-                                 "max_batch_samples": max_batch * 32768, "hbm_budget_bytes": 64 << 30})
+                                 "max_batch_samples": max_batch_samples, "hbm_budget_bytes": 64 << 30})
     # A few distinct reference windows shared round-robin (same shapes and
     # magnitudes as per-vehicle windows; the solve cost does not depend on
     # which window a vehicle tracks).
@@ -185,11 +190,13 @@ def run_fleet(duration_s: float = 5.0, n_vehicles: int = 1000, slots: int = 4, m
     srv.close()
     lat = np.array(lat) if lat else np.array([np.nan])
     return {"workload": f"{n} vehicles at {rate_hz:g} Hz (Poisson), K in {{2048,8192,32768}}, N in {{50,100}}, "
-                        f"32 spheres each, {slots} slots x batch <= {max_batch}",
+                        f"32 spheres each, {slots} slots, batches of what is queued up to {max_batch_samples} "
+                        f"samples",
             "duration_s": duration_s, "solves_per_s": done_n / duration_s,
             "rollout_steps_per_s": done_steps / duration_s,
             "latency_ms": {"p50": float(np.percentile(lat, 50) / 1e3), "p99": float(np.percentile(lat, 99) / 1e3)},
             "offered_per_s": n * rate_hz, "ticks": int(ticks), "missed_ticks": int(missed),
             "rejected": int(rejected), "queue_capacity": queue_capacity,
             "mean_batch": float(np.mean(bsizes)) if bsizes else 0.0,
-            "batches": int(st["batches"])}
+            "p99_batch": float(np.percentile(bsizes, 99)) if bsizes else 0.0,
+            "batches": int(st["batches"]), "dispatcher_host_cores": 1}
