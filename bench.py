@@ -336,7 +336,11 @@ def run_fleet(args, rank: int, peaks: dict, clk: ClockSampler):
     solver = mppi.Solver(p0["model"], p0["params"], cap)
     stream = torch.cuda.current_stream()
     t_tune = time.perf_counter()
-    shape = solver.autotune_batch(fleet.dicts(bufs), stream=stream)
+    if args.shape:
+        shape = tuple(float(v) if i == 3 else int(v) for i, v in enumerate(args.shape.split(",")))
+        solver.set_shape(*shape)
+    else:
+        shape = solver.autotune_batch(fleet.dicts(bufs), stream=stream)
     t_tune = time.perf_counter() - t_tune
     pairs = torch.zeros(1, dtype=torch.int64, device="cuda")
     solver.set_counters(pairs)  # evaluated obstacle pairs of step 0, in an untimed launch
@@ -489,7 +493,7 @@ def reference_windows(n_steps: int):
     return np.stack([traj.window(DT_HEAD * t, N_HEAD, DT_HEAD) for t in range(n_steps)])
 
 
-def run_closed_loop(n_steps: int, peaks: dict, warmup=5):
+def run_closed_loop(n_steps: int, peaks: dict, warmup=5, shape=None):
     """One vehicle, K=16384, N=100, 64 spheres: closed loop on device
     buffers, one solve per control step (CUDA events per solve, L2 flushed
     between), then the same loop through mppi_solve with host buffers."""
@@ -508,9 +512,12 @@ def run_closed_loop(n_steps: int, peaks: dict, warmup=5):
     u_cmd = torch.zeros(4, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     solver = mppi.Solver(prob["model"], prob["params"])
-    shape = solver.autotune_on({"x_hat": x[0], "ref": refs[0], "obstacles": obs, "u_nom": u[0], "K": K_HEAD,
-                                "N": N_HEAD, "dt": DT_HEAD, "lambda": prob["params"]["lambda"],
-                                "sigma": prob["params"]["sigma"], "seed": prob["params"]["seed"], "iter": 0})
+    if shape:
+        solver.set_shape(*shape)
+    else:
+        shape = solver.autotune_on({"x_hat": x[0], "ref": refs[0], "obstacles": obs, "u_nom": u[0], "K": K_HEAD,
+                                    "N": N_HEAD, "dt": DT_HEAD, "lambda": prob["params"]["lambda"],
+                                    "sigma": prob["params"]["sigma"], "seed": prob["params"]["seed"], "iter": 0})
     flush = flusher()
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_total)]
@@ -574,7 +581,7 @@ def run_closed_loop(n_steps: int, peaks: dict, warmup=5):
 
 # ----------------------------------------------------------------- stress
 
-def run_stress(peaks: dict, reps=3):
+def run_stress(peaks: dict, reps=3, shape=None):
     """K=262144, N=200, dt=0.005, 512 spheres + 512 pillars: one solve per
     repetition on device buffers with the instance-autotuned shape; the
     outputs of the last solve are kept for the oracle comparison."""
@@ -589,9 +596,12 @@ def run_stress(peaks: dict, reps=3):
     out = {k: torch.zeros(n, device=dev) for k, n in (("u_out", (N, 4)), ("u_cmd", 4), ("u_next", (N, 4)),
                                                        ("x_next", 13), ("costs", K))}
     s = mppi.Solver(prob["model"], prob["params"])
-    shape = s.autotune_on({"x_hat": x, "ref": r, "obstacles": o, "u_nom": u, "K": K, "N": N,
-                           "dt": prob["params"]["dt"], "lambda": prob["params"]["lambda"],
-                           "sigma": prob["params"]["sigma"], "seed": prob["params"]["seed"], "iter": 0})
+    if shape:
+        s.set_shape(*shape)
+    else:
+        shape = s.autotune_on({"x_hat": x, "ref": r, "obstacles": o, "u_nom": u, "K": K, "N": N,
+                               "dt": prob["params"]["dt"], "lambda": prob["params"]["lambda"],
+                               "sigma": prob["params"]["sigma"], "seed": prob["params"]["seed"], "iter": 0})
     pairs = torch.zeros(1, dtype=torch.int64, device=dev)
     s.set_counters(pairs)
     s.solve_async(x, r, o, u, prob["iter"], u_out=out["u_out"])
@@ -902,6 +912,8 @@ def main():
     ap.add_argument("--serve-vehicles", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="only the headline fleet and its end-to-end figure")
     ap.add_argument("--no-oracle", action="store_true", help="skip the stress workload's FP64 oracle comparison")
+    ap.add_argument("--shape", default="", help="fleet launch shape 'block,lanes,pipelined,margin' instead of the "
+                                                "batch autotuner's (profiling aid)")
     ap.add_argument("--section", default="all",
                     choices=["all", "fleet", "closed_loop", "stress", "serving", "paper", "options", "plain"],
                     help="run one section alone and print its JSON (profiling aid)")
@@ -928,9 +940,11 @@ def main():
     peaks = mppi.measure_peaks()
 
     if args.section != "all":
+        forced = tuple(float(v) if i == 3 else int(v) for i, v in enumerate(args.shape.split(","))) \
+            if args.shape else None
         fn = {"fleet": lambda: run_fleet(args, rank, peaks, clk)["ms"].tolist(),
-              "closed_loop": lambda: run_closed_loop(args.steps, peaks),
-              "stress": lambda: run_stress(peaks)[0], "serving": lambda: run_serving(args),
+              "closed_loop": lambda: run_closed_loop(args.steps, peaks, shape=forced),
+              "stress": lambda: run_stress(peaks, shape=forced)[0], "serving": lambda: run_serving(args),
               "paper": run_paper_point, "options": run_options, "plain": run_plain_step}
         out = fn[args.section]()
         clk.stop()

@@ -1235,10 +1235,20 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             const int T = sI.n_tiles;
             const int stride = partial_stride(N);
             const float* P0 = a.partials + sI.part_off;
+            // When the instance has at most spb tiles, every tile's header
+            // (rho_t, eta_t) is read once into shared memory and the merge
+            // scales s_t stay there; otherwise they go through the partials.
+            const bool fast = T <= spb;
             // rho = min rho_t (FP64 header of each partial)
             double m = INFINITY;
-            for (int t = tid; t < T; t += nthreads)
-                m = fmin(m, __ldcg(reinterpret_cast<const double*>(P0 + (long long)t * stride)));
+            for (int t = tid; t < T; t += nthreads) {
+                const double rt = __ldcg(reinterpret_cast<const double*>(P0 + (long long)t * stride));
+                if (fast) {
+                    sS[t] = rt;
+                    sE[t] = __ldcg(P0 + (long long)t * stride + 2);
+                }
+                m = fmin(m, rt);
+            }
             m = warp_min_d(m);
             if (wlane == 0) s_redd[warp] = m;
             __syncthreads();
@@ -1249,16 +1259,19 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             }
             __syncthreads();
             const double rho = s_rho;
-            // s_t = exp(-(rho_t - rho)/lambda), kept in the partial's pad
-            // slot; eta = sum_t s_t eta_t.
+            // s_t = exp(-(rho_t - rho)/lambda), kept in shared memory (fast)
+            // or in the partial's pad slot; eta = sum_t s_t eta_t.
             float* Pw = a.partials + sI.part_off;
             float eacc = 0.0f;
             for (int t = tid; t < T; t += nthreads) {
-                const double rt = __ldcg(reinterpret_cast<const double*>(P0 + (long long)t * stride));
+                const double rt =
+                    fast ? sS[t] : __ldcg(reinterpret_cast<const double*>(P0 + (long long)t * stride));
+                const float et = fast ? sE[t] : __ldcg(P0 + (long long)t * stride + 2);
                 const float xarg = (float)((rt - rho) / (double)lambda);
                 const float st = (rt < INFINITY && xarg <= kMaxExpArg) ? expf(-xarg) : 0.0f;
-                __stcg(Pw + (long long)t * stride + 3, st);
-                eacc = fmaf(st, __ldcg(P0 + (long long)t * stride + 2), eacc);
+                if (fast) sE[t] = st;
+                else __stcg(Pw + (long long)t * stride + 3, st);
+                eacc = fmaf(st, et, eacc);
             }
             eacc = warp_sum(eacc);
             __syncthreads();
@@ -1287,7 +1300,8 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int t0 = 0; t0 < T; t0 += spb) {
                     const int ch = min(spb, T - t0);
-                    for (int i = tid; i < ch; i += nthreads) sE[i] = __ldcg(P0 + (long long)(t0 + i) * stride + 3);
+                    if (!fast)
+                        for (int i = tid; i < ch; i += nthreads) sE[i] = __ldcg(P0 + (long long)(t0 + i) * stride + 3);
                     __syncthreads();
                     if (warp == 0) {
                         int base = 0;
@@ -1338,16 +1352,8 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                     if (sI.u_out) sI.u_out[o] = v;
                 }
             }
-            __syncthreads();
-            // Warm start: shift by alpha steps with linear interpolation.
-            if (sI.u_next) {
-                const float al = C.shift_alpha;
-                for (int o = tid; o < 4 * N; o += nthreads) {
-                    const int j = o >> 2, c = o & 3;
-                    const float later = (j + 1 < N) ? sunew[o + 4] : (C.tail_mode == 1 ? sunew[o] : Mdl.u_init[c]);
-                    sI.u_next[o] = al == 1.0f ? later : fmaf(al, later - sunew[o], sunew[o]);
-                }
-            }
+            // ApplyToSystem(u_nom_0) by the thread that formed u_out_0
+            // (j = 0 above), while the others go on to the warm start.
             if (tid == 0) {
                 // ApplyToSystem(u_nom_0): feasible command from x_hat.
                 State xh;
@@ -1377,6 +1383,16 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 if (sI.iter_dev) *sI.iter_dev = iter + 1ull;
                 a.done[inst] = 0u;
                 a.errflags[inst] = 0u;
+            }
+            __syncthreads();
+            // Warm start: shift by alpha steps with linear interpolation.
+            if (sI.u_next) {
+                const float al = C.shift_alpha;
+                for (int o = tid; o < 4 * N; o += nthreads) {
+                    const int j = o >> 2, c = o & 3;
+                    const float later = (j + 1 < N) ? sunew[o + 4] : (C.tail_mode == 1 ? sunew[o] : Mdl.u_init[c]);
+                    sI.u_next[o] = al == 1.0f ? later : fmaf(al, later - sunew[o], sunew[o]);
+                }
             }
         }
         __syncthreads();
