@@ -66,7 +66,11 @@ MUFU_PER_PAIR = {"ex2_ops": 1}
 # the kernel in an ncu capture of the named workload, valid only for the
 # kernel source it was taken with (sha256 of the kernel file and its header,
 # first 16 hex digits); any other source reports null.
-TRAFFIC_CAPTURES = {}
+TRAFFIC_CAPTURES = {
+    "fleet": {"kernel_sha": "7c5103e4864177b5", "bytes": 2228224},
+    "closed_loop": {"kernel_sha": "7c5103e4864177b5", "bytes": 119296},
+    "stress": {"kernel_sha": "7c5103e4864177b5", "bytes": 124928},
+}
 KERNEL_FILES = ("paper_2407_09812_gb300/csrc/mppi_kernels.cu", "paper_2407_09812_gb300/csrc/mppi_internal.h")
 
 

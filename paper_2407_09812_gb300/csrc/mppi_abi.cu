@@ -487,7 +487,22 @@ static int tune_on(mppi_ctx* h, mppi_instance in, cudaStream_t st, mppi_shape* b
     int rc = MPPI_OK;
     auto time_shape = [&](const Shape& s) {
         if (smem_bytes(in.N, in.M, s) > 227 * 1024) return;
-        if ((rc = launch_single(h, in, s, st))) return;  // warm-up
+        // A candidate whose warm-up launch (and a second one: the first
+        // may include loading the kernel) takes more than twice the best
+        // so far is not timed further.
+        for (int probe = 0; probe < 2; ++probe) {
+            cudaEventRecord(e0, st);
+            if ((rc = launch_single(h, in, s, st))) return;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = MPPI_ECUDA;
+                return;
+            }
+            float first = 0.0f;
+            cudaEventElapsedTime(&first, e0, e1);
+            if (first <= 2.0f * bestT / 5.0f) break;
+            if (probe == 1) return;
+        }
         cudaEventRecord(e0, st);
         for (int r = 0; r < 5; ++r) launch_single(h, in, s, st);
         cudaEventRecord(e1, st);
@@ -1064,10 +1079,25 @@ int mppi_autotune_batch(mppi_handle h, const mppi_instance* instances, int32_t n
     int rc = MPPI_OK;
     auto time_shape = [&](const Shape& s) {
         h->forced = s;
-        if ((rc = mppi_solve_batch(h, ins.data(), n, st))) {
-            // A shape whose shared memory does not fit is skipped.
-            if (rc == MPPI_EINVAL) rc = MPPI_OK;
-            return;
+        // Warm-up launch, timed: a candidate that takes more than twice the
+        // best so far (twice: the first launch may include loading the
+        // kernel) is not timed further.
+        for (int probe = 0; probe < 2; ++probe) {
+            cudaEventRecord(e0, st);
+            if ((rc = mppi_solve_batch(h, ins.data(), n, st))) {
+                // A shape whose shared memory does not fit is skipped.
+                if (rc == MPPI_EINVAL) rc = MPPI_OK;
+                return;
+            }
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = MPPI_ECUDA;
+                return;
+            }
+            float first = 0.0f;
+            cudaEventElapsedTime(&first, e0, e1);
+            if (first <= 2.0f * bestT / 3.0f) break;
+            if (probe == 1) return;
         }
         cudaEventRecord(e0, st);
         for (int r = 0; r < 3; ++r) mppi_solve_batch(h, ins.data(), n, st);
