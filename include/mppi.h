@@ -293,7 +293,10 @@ typedef struct {
                                dynamics thread and `lanes` cost threads in
                                separate warps, handing states over through
                                shared-memory rings (block / (1 + lanes)
-                               samples per block)                           */
+                               samples per block); 2: in addition a noise
+                               thread per sample in its own warp that draws
+                               the noise ahead of the dynamics thread
+                               (block / (2 + lanes) samples per block)      */
     float list_margin;      /* obstacle tiling: a warp's kept-obstacle list
                                covers the box of its positions grown by
                                this many metres and is reused while they

@@ -297,7 +297,7 @@ DevInstance make_instance(const mppi_ctx* h, const mppi_instance& in, Shape s) {
     d.iter_dev = reinterpret_cast<unsigned long long*>(in.iter_dev);
     d.iter = in.iter;
     d.K = in.K; d.N = in.N; d.M = in.M;
-    const int spb = s.pipe ? s.block / (1 + s.lanes) : s.block / s.lanes;
+    const int spb = s.pipe ? s.block / (s.pipe + s.lanes) : s.block / s.lanes;
     d.n_tiles = (in.K + spb - 1) / spb;
     d.dt = in.dt; d.lambda = in.lambda;
     for (int c = 0; c < 4; ++c) d.sigma[c] = in.sigma[c];
@@ -384,7 +384,7 @@ int plan_batch(mppi_ctx* h, const mppi_instance* ins, int n, BatchPlan* plan) {
         Mmax = std::max(Mmax, ins[i].M);
     }
     Shape s = choose_shape(h, sumK / n, Nmax, Mmax, sumK);
-    const int spb = s.pipe ? s.block / (1 + s.lanes) : s.block / s.lanes;
+    const int spb = s.pipe ? s.block / (s.pipe + s.lanes) : s.block / s.lanes;
     long long tiles = 0;
     size_t pf = 0;
     for (int i = 0; i < n; ++i) {
@@ -465,6 +465,8 @@ static std::vector<Shape> tuning_candidates() {
             if (b / l >= 8) cands.push_back(Shape{b, l, 0, 0.0f});
     for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 1, 0.0f});
     for (int b : {192, 384}) cands.push_back(Shape{b, 2, 1, 0.0f});
+    for (int b : {192, 384}) cands.push_back(Shape{b, 1, 2, 0.0f});
+    for (int b : {256, 512}) cands.push_back(Shape{b, 2, 2, 0.0f});
     return cands;
 }
 

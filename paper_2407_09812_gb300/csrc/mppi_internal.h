@@ -94,7 +94,7 @@ struct DevInstance {
 struct Shape {
     int block;     // threads per block
     int lanes;     // lanes per sample
-    int pipe;      // 1: pipelined (a dynamics thread and a cost thread per sample)
+    int pipe;      // 1: pipelined (a dynamics thread and cost lanes per sample); 2: also a noise thread
     float margin;  // kept-obstacle list margin [m]; 0: the default of the form
 };
 

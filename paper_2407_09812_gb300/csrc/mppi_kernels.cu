@@ -762,7 +762,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 // The pipelined variant adds, per pair of (dynamics, cost) warps, a ring of
 // kRing slots (kSlotF4 float4 per lane, stored lane-contiguous: the position
 // and the step's tracking cost, the position's compensation terms, and the
-// control) and four mbarriers per slot (two used: full / empty).
+// control) and four mbarriers per slot: [2] / [3] full / empty of that ring,
+// [0] / [1] full / empty of the noise ring (one float4 per lane and slot)
+// that the noise warp of the PIPE == 2 form fills.
 constexpr int kRing = 4;
 constexpr int kSlotF4 = 3;
 // States the cost lanes of the pipelined form score per pass over their
@@ -770,14 +772,14 @@ constexpr int kSlotF4 = 3;
 constexpr int kStatesPerPass = 2;
 
 struct SmemLayout {
-    unsigned obs, ref, u, S, e, list, part, wlist, xring, bars, total;
+    unsigned obs, ref, u, S, e, list, part, wlist, xring, nring, bars, total;
 };
 
 __host__ __device__ inline unsigned align_up(unsigned v, unsigned a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int block, int lanes, bool pipe) {
+__host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int block, int lanes, int pipe) {
     SmemLayout L;
-    const int spb = pipe ? block / (1 + lanes) : block / lanes;
+    const int spb = pipe ? block / (pipe + lanes) : block / lanes;
     const int npart = block > N_max ? block : N_max;
     const unsigned slots = pipe ? (unsigned)(spb / 32) * kRing * 32u : 0u;
     unsigned o = 0;
@@ -790,6 +792,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
     L.wlist = o; o = align_up(o + 48u * (unsigned)block, 128);  // 96 float4 (32 obstacle pairs) per warp
     L.xring = o; o = align_up(o + 16u * kSlotF4 * slots, 128);
+    L.nring = o; o = align_up(o + (pipe == 2 ? 16u * slots : 0u), 128);
     L.bars = o;  o = align_up(o + 8u * 4u * (slots / 32u), 128);
     L.total = o;
     return L;
@@ -804,7 +807,7 @@ constexpr float kMaxExpArg = 104.0f;
 // MINB > 1: an instantiation for blocks of at most 128 threads compiled to
 // fit MINB blocks per SM (a register budget of 65536 / (128 MINB) per
 // thread), for launches that fill the GPU and are bound by issue rate.
-template <int LANES, bool PIPE, int MINB>
+template <int LANES, int PIPE, int MINB>
 __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(const LaunchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long mbar;
@@ -819,12 +822,12 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
 
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
-    // PIPE: samples [0, spb) have a dynamics thread (tid < spb) and LANES
-    // cost lanes (tid >= spb) in separate warps; otherwise LANES lanes per
-    // sample.
-    const int spb = PIPE ? nthreads / (1 + LANES) : nthreads / LANES;
-    const int group = PIPE ? (tid < spb ? tid : (tid - spb) / LANES) : tid / LANES;
-    const int lane = PIPE ? (tid < spb ? 0 : (tid - spb) % LANES) : tid % LANES;
+    // PIPE 1: samples [0, spb) have a dynamics thread (tid < spb) and LANES
+    // cost lanes (tid >= spb) in separate warps; PIPE 2: also a noise thread
+    // (spb <= tid < 2 spb); otherwise LANES lanes per sample.
+    const int spb = PIPE ? nthreads / (PIPE + LANES) : nthreads / LANES;
+    const int group = PIPE ? (tid < PIPE * spb ? tid % spb : (tid - PIPE * spb) / LANES) : tid / LANES;
+    const int lane = PIPE ? (tid < PIPE * spb ? 0 : (tid - PIPE * spb) % LANES) : tid % LANES;
     const int warp = tid >> 5, wlane = tid & 31, nwarps = nthreads >> 5;
 
     const SmemLayout L = smem_layout(a.N_max, a.M_max, nthreads, LANES, PIPE);
@@ -952,7 +955,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
         __syncthreads();
 
         // --------------------------------------------------- rollouts
-        if constexpr (!PIPE) {
+        if constexpr (PIPE == 0) {
             const int k_raw = tile * spb + group;
             const bool valid = k_raw < K;
             const unsigned k = (unsigned)(valid ? k_raw : K - 1);
@@ -1006,16 +1009,18 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             __syncthreads();
         } else {
             // Pipelined rollout.  The dynamics thread of a sample draws the
-            // noise (one step ahead, overlapping the RK4 chain), clamps the
-            // control, runs the constraint pipeline and RK4 and forms the
-            // step's tracking cost; it hands the new position (with its
-            // compensation terms), that cost and the control to the sample's
-            // cost lanes through a ring in shared memory.  The cost lanes add
-            // the input and input-change cost and score the positions, two
-            // states per pass, against the obstacles and the grid while the
-            // dynamics thread is already integrating the next steps.  Every
-            // wait is bounded.
-            const bool is_cost = tid >= spb;
+            // noise (one step ahead, overlapping the RK4 chain; with PIPE == 2
+            // a noise thread in its own warp draws it and hands it over
+            // through a second ring), clamps the control, runs the constraint
+            // pipeline and RK4 and forms the step's tracking cost; it hands
+            // the new position (with its compensation terms), that cost and
+            // the control to the sample's cost lanes through a ring in shared
+            // memory.  The cost lanes add the input and input-change cost and
+            // score the positions, two states per pass, against the obstacles
+            // and the grid while the dynamics thread is already integrating
+            // the next steps.  Every wait is bounded.
+            const bool is_cost = tid >= PIPE * spb;
+            const bool is_noise = PIPE == 2 && tid >= spb && !is_cost;
             const int pw = group >> 5;  // warp pair
             float4* xring = reinterpret_cast<float4*>(smem + L.xring);
             const unsigned bars = smem_addr(smem + L.bars);
@@ -1025,6 +1030,10 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             // Field f of this lane's entry in a ring slot.
             auto ring_at = [&](int slot, int f) { return xring + ((pw * kRing + slot) * kSlotF4 + f) * 32 + (group & 31); };
             constexpr int X_FULL = 2, X_EMPTY = 3;
+            // Noise ring (PIPE == 2): delta for step g in slot g % kRing.
+            float4* nring = reinterpret_cast<float4*>(smem + L.nring);
+            auto nring_at = [&](int slot) { return nring + (pw * kRing + slot) * 32 + (group & 31); };
+            constexpr int N_FULL = 0, N_EMPTY = 1;
             const int k_raw = tile * spb + group;
             const bool valid = k_raw < K;
             const unsigned k = (unsigned)(valid ? k_raw : K - 1);
@@ -1033,15 +1042,36 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             x.qy = s_x0[5]; x.qz = s_x0[6]; x.vx = s_x0[7]; x.vy = s_x0[8]; x.vz = s_x0[9];
             x.wx = s_x0[10]; x.wy = s_x0[11]; x.wz = s_x0[12];
             Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (!is_cost) {
+            if (is_noise) {
+                // Noise thread (PIPE == 2): draws delta for every step ahead of
+                // the dynamics thread and hands it over through its own ring.
                 const PhiloxPre ppre = philox_pre_sample(k, iter, s_rk);
-                float4 d_next = noise_delta(normals4_pre(0u, ppre, &s_pt, s_rk), sigma);
                 for (int j = 0; j < N; ++j) {
                     const unsigned g = g_run + (unsigned)j;
                     const int slot = slot_of(g);
                     const unsigned ph = (g / kRing) & 1u;
-                    const float4 d = d_next;
-                    d_next = noise_delta(normals4_pre((unsigned)min(j + 1, N - 1), ppre, &s_pt, s_rk), sigma);
+                    const float4 d = noise_delta(normals4_pre((unsigned)j, ppre, &s_pt, s_rk), sigma);
+                    if (g >= (unsigned)kRing) mbar_wait_or_abort(bar_of(slot, N_EMPTY), ph ^ 1u, abort_flag, wait_polls);
+                    *nring_at(slot) = d;
+                    mbar_arrive(bar_of(slot, N_FULL));
+                }
+            } else if (!is_cost) {
+                const PhiloxPre ppre = philox_pre_sample(k, iter, s_rk);
+                float4 d_next = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (PIPE == 1) d_next = noise_delta(normals4_pre(0u, ppre, &s_pt, s_rk), sigma);
+                for (int j = 0; j < N; ++j) {
+                    const unsigned g = g_run + (unsigned)j;
+                    const int slot = slot_of(g);
+                    const unsigned ph = (g / kRing) & 1u;
+                    float4 d;
+                    if (PIPE == 2) {
+                        mbar_wait_or_abort(bar_of(slot, N_FULL), ph, abort_flag, wait_polls);
+                        d = *nring_at(slot);
+                        mbar_arrive(bar_of(slot, N_EMPTY));
+                    } else {
+                        d = d_next;
+                        d_next = noise_delta(normals4_pre((unsigned)min(j + 1, N - 1), ppre, &s_pt, s_rk), sigma);
+                    }
                     const float4 un = su[j];
                     const float4 u = clamp_input(Mdl, perturb(un, d));
                     const Feasible f = feasible(Mdl, x, u, inv_dt);
@@ -1408,9 +1438,10 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
 constexpr int kMinBlocks128 = 6;
 
 bool shape_supported(Shape s) {
-    if (s.pipe == 1) {
-        // A dynamics warp plus `lanes` cost warps per 32 samples.
-        const int unit = 32 * (1 + s.lanes);
+    if (s.pipe == 1 || s.pipe == 2) {
+        // A dynamics warp (and with pipe 2 a noise warp) plus `lanes` cost
+        // warps per 32 samples.
+        const int unit = 32 * (s.pipe + s.lanes);
         return (s.lanes == 1 || s.lanes == 2) && s.block >= unit && s.block <= 512 && s.block % unit == 0;
     }
     const bool lanes_ok = s.lanes == 1 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8 || s.lanes == 32;
@@ -1419,7 +1450,7 @@ bool shape_supported(Shape s) {
 }
 
 size_t smem_bytes(int N_max, int M_max, Shape s) {
-    return smem_layout(N_max, M_max, s.block, s.lanes, s.pipe != 0).total;
+    return smem_layout(N_max, M_max, s.block, s.lanes, s.pipe).total;
 }
 
 // Largest dynamic shared memory opted in so far, per instantiation and per
@@ -1429,7 +1460,7 @@ size_t smem_bytes(int N_max, int M_max, Shape s) {
 // call.
 constexpr int kMaxDevices = 64;
 
-template <int LANES, bool PIPE, int MINB>
+template <int LANES, int PIPE, int MINB>
 static std::atomic<int>* smem_opt_in() {
     static std::atomic<int> v[kMaxDevices] = {};
     int dev = 0;
@@ -1440,7 +1471,7 @@ static std::atomic<int>* smem_opt_in() {
     return &v[dev];
 }
 
-template <int LANES, bool PIPE, int MINB>
+template <int LANES, int PIPE, int MINB>
 static cudaError_t prepare_t(size_t smem) {
     std::atomic<int>* opt = smem_opt_in<LANES, PIPE, MINB>();
     if (opt && (int)smem <= opt->load()) return cudaSuccess;
@@ -1454,7 +1485,7 @@ static cudaError_t prepare_t(size_t smem) {
     return e;
 }
 
-template <int LANES, bool PIPE, int MINB = 1>
+template <int LANES, int PIPE, int MINB = 1>
 static cudaError_t launch_t(const LaunchArgs& a, int block, int grid, size_t smem, cudaStream_t st) {
     cudaError_t e = prepare_t<LANES, PIPE, MINB>(smem);
     if (e != cudaSuccess) return e;
@@ -1465,24 +1496,29 @@ static cudaError_t launch_t(const LaunchArgs& a, int block, int grid, size_t sme
 cudaError_t launch_tiles(const LaunchArgs& args, Shape s, int grid, size_t smem, cudaStream_t st) {
     LaunchArgs a = args;
     a.C.cull_margin = list_margin(s);
-    if (s.pipe) {
-        if (s.lanes == 1) return launch_t<1, true>(a, s.block, grid, smem, st);
-        if (s.lanes == 2) return launch_t<2, true>(a, s.block, grid, smem, st);
+    if (s.pipe == 1) {
+        if (s.lanes == 1) return launch_t<1, 1>(a, s.block, grid, smem, st);
+        if (s.lanes == 2) return launch_t<2, 1>(a, s.block, grid, smem, st);
+        return cudaErrorInvalidValue;
+    }
+    if (s.pipe == 2) {
+        if (s.lanes == 1) return launch_t<1, 2>(a, s.block, grid, smem, st);
+        if (s.lanes == 2) return launch_t<2, 2>(a, s.block, grid, smem, st);
         return cudaErrorInvalidValue;
     }
     switch (s.lanes) {
         case 1:
-            return s.block <= 128 ? launch_t<1, false, kMinBlocks128>(a, s.block, grid, smem, st)
-                                  : launch_t<1, false>(a, s.block, grid, smem, st);
-        case 2: return launch_t<2, false>(a, s.block, grid, smem, st);
-        case 4: return launch_t<4, false>(a, s.block, grid, smem, st);
-        case 8: return launch_t<8, false>(a, s.block, grid, smem, st);
-        case 32: return launch_t<32, false>(a, s.block, grid, smem, st);
+            return s.block <= 128 ? launch_t<1, 0, kMinBlocks128>(a, s.block, grid, smem, st)
+                                  : launch_t<1, 0>(a, s.block, grid, smem, st);
+        case 2: return launch_t<2, 0>(a, s.block, grid, smem, st);
+        case 4: return launch_t<4, 0>(a, s.block, grid, smem, st);
+        case 8: return launch_t<8, 0>(a, s.block, grid, smem, st);
+        case 32: return launch_t<32, 0>(a, s.block, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int LANES, bool PIPE, int MINB = 1>
+template <int LANES, int PIPE, int MINB = 1>
 static int occupancy_t(int block, size_t smem) {
     int n = 0;
     prepare_t<LANES, PIPE, MINB>(smem);
@@ -1493,15 +1529,16 @@ static int occupancy_t(int block, size_t smem) {
 }
 
 int max_active_blocks(Shape s, size_t smem) {
-    if (s.pipe) return s.lanes == 2 ? occupancy_t<2, true>(s.block, smem) : occupancy_t<1, true>(s.block, smem);
+    if (s.pipe == 1) return s.lanes == 2 ? occupancy_t<2, 1>(s.block, smem) : occupancy_t<1, 1>(s.block, smem);
+    if (s.pipe == 2) return s.lanes == 2 ? occupancy_t<2, 2>(s.block, smem) : occupancy_t<1, 2>(s.block, smem);
     switch (s.lanes) {
         case 1:
-            return s.block <= 128 ? occupancy_t<1, false, kMinBlocks128>(s.block, smem)
-                                  : occupancy_t<1, false>(s.block, smem);
-        case 2: return occupancy_t<2, false>(s.block, smem);
-        case 4: return occupancy_t<4, false>(s.block, smem);
-        case 8: return occupancy_t<8, false>(s.block, smem);
-        case 32: return occupancy_t<32, false>(s.block, smem);
+            return s.block <= 128 ? occupancy_t<1, 0, kMinBlocks128>(s.block, smem)
+                                  : occupancy_t<1, 0>(s.block, smem);
+        case 2: return occupancy_t<2, 0>(s.block, smem);
+        case 4: return occupancy_t<4, 0>(s.block, smem);
+        case 8: return occupancy_t<8, 0>(s.block, smem);
+        case 32: return occupancy_t<32, 0>(s.block, smem);
         default: return 1;
     }
 }

@@ -9,7 +9,7 @@ import os
 import numpy as np
 import pytest
 
-from parity import assert_step_close, cost_err
+from parity import assert_step_close, control_err, cost_err
 
 pytestmark = pytest.mark.gpu
 
@@ -133,6 +133,7 @@ def test_every_launch_shape_matches_and_is_deterministic(M, orc, inp):
     shapes += [(64, 32, 0, 0.0), (256, 32, 0, 0.0), (512, 32, 0, 0.0)]
     shapes += [(128, 1, 1, 0.0), (256, 1, 1, 0.0), (512, 1, 1, 0.0), (96, 2, 1, 0.0), (192, 2, 1, 0.0),
                (384, 2, 1, 0.0)]
+    shapes += [(96, 1, 2, 0.0), (192, 1, 2, 0.0), (384, 1, 2, 0.0), (256, 2, 2, 0.0), (512, 2, 2, 0.0)]
     shapes += [(128, 1, 0, 0.25), (128, 4, 0, 3.0), (256, 1, 1, 2.0), (256, 32, 0, 0.5)]
     for shape in shapes:
         a = gpu_solve(M, prob, shape=shape)
@@ -145,18 +146,29 @@ def test_every_launch_shape_matches_and_is_deterministic(M, orc, inp):
 @pytest.mark.parametrize("K,N,Mo", [(16384, 100, 64), (1000, 1, 3), (257, 7, 0), (3000, 37, 40)])
 def test_pipelined_form_matches_one_thread_per_sample(M, orc, inp, K, N, Mo):
     """The pipelined form (dynamics and cost threads per sample, handing
-    states over through mbarrier-guarded rings) gives the per-sample costs
-    of one thread per sample to FP32 rounding (the same arithmetic compiled
-    in two places) and matches the oracle."""
+    states over through mbarrier-guarded rings; with a noise thread too)
+    gives the per-sample costs of one thread per sample to FP32 rounding
+    (the same arithmetic compiled in two places) and matches the oracle."""
     prob = inp.eight_with_spheres(K=K, N=N, M=Mo, t0=0.6, **{"lambda": 200.0})
     if Mo == 0:
         prob["obstacles"] = np.zeros((0, 4), np.float32)
     b = gpu_solve(M, prob, shape=(128, 1, 0))
     ref = orc.mppi_step(prob, n_threads=16)
-    for shape in ((256, 1, 1), (384, 2, 1)):
+    for shape in ((256, 1, 1), (384, 2, 1), (384, 1, 2), (512, 2, 2)):
         a = gpu_solve(M, prob, shape=shape)
         assert cost_err(a["costs"], b["costs"])[0] <= 1e-6
         assert_step_close(prob, a, ref)
+    # The noise thread's form (pipelined = 2) draws the same noise and runs
+    # the same dynamics arithmetic: with the same samples per block its
+    # per-sample costs are bitwise the two-warp form's.  The update is equal
+    # to rounding: the tile's weighted noise sum splits each step's
+    # contributors over (threads per block / N) groups, 384 threads here
+    # against 256.
+    two, three = gpu_solve(M, prob, shape=(256, 1, 1)), gpu_solve(M, prob, shape=(384, 1, 2))
+    assert np.array_equal(two["costs"], three["costs"])
+    sig = prob["params"]["sigma"]
+    for k in ("u_out", "u_next", "u_cmd"):
+        assert control_err(three[k], two[k], sig) <= 1e-6, k
 
 
 def test_closed_loop_full_size(M, orc, inp):
