@@ -710,6 +710,18 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     return ok != 0u;
 }
 
+// Non-blocking test of one phase of the barrier.
+__device__ __forceinline__ bool mbar_test_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
 // Default bound of every device-side wait, in polls of the barrier (each
 // poll may suspend for a hardware-defined time): about a second.
 constexpr long long kWaitPolls = 1ll << 22;
@@ -726,6 +738,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
 // stuck pipeline drains quickly instead of every later wait timing out.
 __device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity, volatile int* abort_flag,
                                                    long long polls) {
+    if (mbar_test_wait(bar, parity)) return true;
     for (long long i = 0; i < polls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 63) == 63 && *abort_flag) return false;
@@ -901,20 +914,29 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             bulk_load(smem_addr(sobs), sI.obs, 16u * (unsigned)M, bar);
         if (tid == 0 && (lost || s_abort)) atomicOr(&a.errflags[inst], ERR_TIMEOUT);
         if (tid < 13) s_xhat[tid] = sI.x_hat[tid];
-        __syncthreads();
-        // Origin shift to the state estimate's position: translation
-        // invariant in exact arithmetic, keeps FP32 positions small.
-        const float p0x = s_xhat[0], p0y = s_xhat[1], p0z = s_xhat[2];
+        // The reference window and the nominal are loaded alongside x_hat
+        // (no dependent round trip); the reference positions are shifted
+        // once x_hat is in shared memory, each row by the thread that
+        // loaded it.
         for (int j = tid; j <= N; j += nthreads) {
             const float* r = sI.ref + 13 * (size_t)j;
-            sref[4 * j + 0] = make_float4(r[0] - p0x, r[1] - p0y, r[7], r[8]);
-            sref[4 * j + 1] = make_float4(r[2] - p0z, r[9], r[10], r[11]);
+            sref[4 * j + 0] = make_float4(r[0], r[1], r[7], r[8]);
+            sref[4 * j + 1] = make_float4(r[2], r[9], r[10], r[11]);
             sref[4 * j + 2] = make_float4(r[3], r[4], r[5], r[6]);
             sref[4 * j + 3] = make_float4(r[12], 0.0f, 0.0f, 0.0f);
         }
         for (int j = tid; j < N; j += nthreads) {
             const float* u = sI.u_nom + 4 * (size_t)j;
             su[j] = make_float4(u[0], u[1], u[2], u[3]);
+        }
+        __syncthreads();
+        // Origin shift to the state estimate's position: translation
+        // invariant in exact arithmetic, keeps FP32 positions small.
+        const float p0x = s_xhat[0], p0y = s_xhat[1], p0z = s_xhat[2];
+        for (int j = tid; j <= N; j += nthreads) {
+            sref[4 * j + 0].x -= p0x;
+            sref[4 * j + 0].y -= p0y;
+            sref[4 * j + 1].x -= p0z;
         }
         if (tid == 0) {
             State x;
