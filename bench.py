@@ -67,9 +67,9 @@ MUFU_PER_PAIR = {"ex2_ops": 1}
 # kernel source it was taken with (sha256 of the kernel file and its header,
 # first 16 hex digits); any other source reports null.
 TRAFFIC_CAPTURES = {
-    "fleet": {"kernel_sha": "7c5103e4864177b5", "bytes": 2228224},
-    "closed_loop": {"kernel_sha": "7c5103e4864177b5", "bytes": 119296},
-    "stress": {"kernel_sha": "7c5103e4864177b5", "bytes": 124928},
+    "fleet": {"kernel_sha": "3d01e3c0f082118a", "bytes": 2230528},
+    "closed_loop": {"kernel_sha": "3d01e3c0f082118a", "bytes": 119808},
+    "stress": {"kernel_sha": "3d01e3c0f082118a", "bytes": 166400},
 }
 KERNEL_FILES = ("paper_2407_09812_gb300/csrc/mppi_kernels.cu", "paper_2407_09812_gb300/csrc/mppi_internal.h")
 
