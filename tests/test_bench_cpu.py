@@ -76,3 +76,22 @@ def test_host_instance_records_match_the_arrays():
     short = dict(dicts[0], ref=np.zeros((3, 13), np.float32))
     with pytest.raises(ValueError):
         mppi.host_instances([short])
+
+
+def test_roofline_arithmetic():
+    """The roofline entry: algorithmic flop over the launch time against the
+    measured FFMA rate, and the MUFU fraction as the time the launch's MUFU
+    work needs at the measured rates over the launch time."""
+    import bench
+    peaks = {"fp32_flops": 80e12, "ex2_ops": 10e12, "lg2_ops": 5e12, "rsqrt_ops": 5e12, "sin_ops": 5e12,
+             "cos_ops": 5e12}
+    steps, pairs, ms = 1e8, 2e8, 4.0
+    flop = steps * bench.FLOP_PER_STEP + pairs * bench.FLOP_PER_PAIR
+    r = bench.roofline(flop, bench.mufu_ops(steps, pairs), ms, peaks, 12345, "test")
+    assert r["achieved"] == pytest.approx(flop / 4e-3 / 1e12)
+    assert r["peak"] == pytest.approx(80.0) and r["frac"] == pytest.approx(r["achieved"] / 80.0)
+    mufu_s = (2 * steps + 3 * steps + 2 * steps) / 5e12 + 2 * steps / 5e12 + pairs / 10e12
+    assert r["mufu"]["frac"] == pytest.approx(mufu_s / 4e-3)
+    assert r["traffic"] == 12345 and r["bound"] == "alu"
+    # Traffic is reported only for the kernel source it was captured with.
+    assert bench.captured_traffic("no such workload") is None
