@@ -26,8 +26,13 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the MPPI library")
 
 
+# Host code: OpenMP for the host-buffer batch's packing (ignored where the
+# host compiler lacks it; the loops then run on one thread).
+HOST_OMP = ["-Xcompiler", "-fopenmp"]
+
+
 def _flags(verbose_ptx: bool):
-    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+    f = ARCH + HOST_OMP + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                 "--expt-relaxed-constexpr", "-I", os.path.join(os.path.dirname(HERE), "include")]
     if verbose_ptx:
         f += ["-Xptxas", "-v"]
@@ -67,7 +72,7 @@ def build(force: bool = False, verbose_ptx: bool = False, quiet: bool = True) ->
                 sys.stderr.write(log)
     objs = [o for o, _ in results]
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread", "-ldl", "-lrt"]
+    cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + HOST_OMP + ["-Xcompiler", "-fPIC", "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")

@@ -947,10 +947,24 @@ int mppi_solve_batch_host(mppi_handle h, const mppi_instance* instances, int32_t
     float* hb = h->h_bio;
     float* db = h->d_bio;
     std::vector<mppi_instance> dev((size_t)n);
-    size_t oi = 0, oo = in_f;
+    std::vector<size_t> ois((size_t)n), oos((size_t)n);
+    {
+        size_t oi = 0, oo = in_f;
+        for (int i = 0; i < n; ++i) {
+            const size_t N = (size_t)instances[i].N, M = (size_t)instances[i].M;
+            ois[(size_t)i] = oi;
+            oos[(size_t)i] = oo;
+            oi += 16 + up4(13 * (N + 1)) + 4 * M + 4 * N;
+            oo += 8 * N + 24 + (instances[i].costs ? up4((size_t)instances[i].K) : 0);
+        }
+    }
+    // Packing and unpacking are plain copies per instance: on a few host
+    // threads when the batch is large (OpenMP; one thread without it).
+#pragma omp parallel for schedule(static) num_threads(n >= 64 ? 8 : 1)
     for (int i = 0; i < n; ++i) {
         const mppi_instance& in = instances[i];
         const size_t N = (size_t)in.N, M = (size_t)in.M;
+        size_t oi = ois[(size_t)i], oo = oos[(size_t)i];
         mppi_instance& d = dev[(size_t)i];
         d = in;
         std::memcpy(hb + oi, in.x_hat, 13 * sizeof(float));
@@ -964,7 +978,6 @@ int mppi_solve_batch_host(mppi_handle h, const mppi_instance* instances, int32_t
         oi += 4 * M;
         std::memcpy(hb + oi, in.u_nom, 4 * N * sizeof(float));
         d.u_nom = db + oi;
-        oi += 4 * N;
         d.u_out = db + oo;
         d.u_cmd = db + oo + 4 * N;
         d.u_next = db + oo + 4 * N + 4;
@@ -972,7 +985,6 @@ int mppi_solve_batch_host(mppi_handle h, const mppi_instance* instances, int32_t
         d.status = reinterpret_cast<int32_t*>(db + oo + 8 * N + 20);
         oo += 8 * N + 24;
         d.costs = in.costs ? db + oo : nullptr;
-        if (in.costs) oo += up4((size_t)in.K);
     }
     if (cudaMemcpyAsync(db, hb, in_f * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) return MPPI_ECUDA;
     int rc = mppi_solve_batch_graph(h, dev.data(), n, st);
@@ -987,12 +999,12 @@ int mppi_solve_batch_host(mppi_handle h, const mppi_instance* instances, int32_t
     while ((q = cudaEventQuery(h->ev_io)) == cudaErrorNotReady) {
     }
     if (q != cudaSuccess) return MPPI_ECUDA;
-    int first = MPPI_OK;
-    oo = in_f;
+    std::vector<int32_t> sts((size_t)n);
+#pragma omp parallel for schedule(static) num_threads(n >= 64 ? 8 : 1)
     for (int i = 0; i < n; ++i) {
         const mppi_instance& in = instances[i];
         const size_t N = (size_t)in.N;
-        const float* o = hb + oo;
+        const float* o = hb + oos[(size_t)i];
         if (in.u_out) std::memcpy(in.u_out, o, 4 * N * sizeof(float));
         if (in.u_cmd) std::memcpy(in.u_cmd, o + 4 * N, 4 * sizeof(float));
         if (in.u_next) std::memcpy(in.u_next, o + 4 * N + 4, 4 * N * sizeof(float));
@@ -1000,13 +1012,11 @@ int mppi_solve_batch_host(mppi_handle h, const mppi_instance* instances, int32_t
         int32_t status;
         std::memcpy(&status, o + 8 * N + 20, sizeof(status));
         if (in.status) *in.status = status;
-        if (status != MPPI_OK && first == MPPI_OK) first = status;
-        oo += 8 * N + 24;
-        if (in.costs) {
-            std::memcpy(in.costs, hb + oo, (size_t)in.K * sizeof(float));
-            oo += up4((size_t)in.K);
-        }
+        sts[(size_t)i] = status;
+        if (in.costs) std::memcpy(in.costs, o + 8 * N + 24, (size_t)in.K * sizeof(float));
     }
+    int first = MPPI_OK;
+    for (int i = 0; i < n && first == MPPI_OK; ++i) first = sts[(size_t)i];
     return first;
 }
 
