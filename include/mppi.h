@@ -272,6 +272,22 @@ typedef struct {
  * state the roofline against rates measured on the GPU itself. */
 int mppi_measure_peaks(mppi_peaks* out, void* stream);
 
+/* The sampling step of Sec. III-A (Eq. rollout_computation: delta u_{k,j}
+ * ~ N(0, Sigma), Sigma = diag(sigma^2)) by itself, exactly as the rollouts
+ * of a solve with these parameters and iteration count draw it:
+ * Philox4x32-10 on the counter (k, j, iter) under the key (seed,
+ * stream_id), Box-Muller, times sigma.  Writes delta for samples
+ * k0 .. k0 + K - 1 and steps 0 .. N - 1 to out[((k - k0) N + j) 4 + c]
+ * (device pointer, 16-byte aligned, K N 4 floats), asynchronously on
+ * `stream`.  The paper has no call of its own for this; it exposes the
+ * noise so that it can be compared with an independent implementation
+ * element by element.  Of params only sigma, seed and stream_id are used
+ * (the whole struct is validated).  Returns MPPI_EINVAL for a NULL or
+ * misaligned pointer, invalid params, K or N < 1, K > MPPI_K_MAX,
+ * N > MPPI_N_MAX or k0 + K > 2^32; MPPI_ECUDA if the launch fails. */
+int mppi_sample_noise(const mppi_params* params, uint64_t iter, uint32_t k0, int32_t K, int32_t N,
+                      float* out, void* stream);
+
 /* Failure-path hook (the paper has no counterpart).  Every device-side wait
  * of the kernel (the obstacle staging copy, the pipelined form's state
  * ring) is a bounded poll of an mbarrier; polls sets that bound for this

@@ -687,6 +687,18 @@ int mppi_set_counters(mppi_handle h, uint64_t* counters) {
     return MPPI_OK;
 }
 
+int mppi_sample_noise(const mppi_params* params, uint64_t iter, uint32_t k0, int32_t K, int32_t N, float* out,
+                      void* stream) {
+    if (!params || !out || !aligned16(out) || check_params(params) != MPPI_OK) return MPPI_EINVAL;
+    if (K < 1 || N < 1 || K > MPPI_K_MAX || N > MPPI_N_MAX) return MPPI_EINVAL;
+    if ((uint64_t)k0 + (uint64_t)K > (1ull << 32)) return MPPI_EINVAL;
+    const unsigned key0 = (unsigned)(params->seed & 0xffffffffu);
+    const unsigned key1 = (unsigned)(params->seed >> 32) ^ params->stream_id;
+    const cudaError_t e = launch_noise(out, k0, K, N, iter, key0, key1, params->sigma,
+                                       static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MPPI_OK : MPPI_ECUDA;
+}
+
 int mppi_set_wait_limit(mppi_handle h, int64_t polls, int32_t stall_obstacle_copy) {
     if (!h || polls < 0) return MPPI_EINVAL;
     h->wait_polls = polls;

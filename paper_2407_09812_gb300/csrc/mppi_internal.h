@@ -142,5 +142,8 @@ bool shape_supported(Shape s);
 cudaError_t launch_tiles(const LaunchArgs& a, Shape s, int grid, size_t smem, cudaStream_t st);
 int max_active_blocks(Shape s, size_t smem);
 int sm_count();
+// delta of samples k0 .. k0 + K - 1, steps 0 .. N - 1 into out (16-byte aligned, K N float4).
+cudaError_t launch_noise(float* out, unsigned k0, int K, int N, unsigned long long iter, unsigned key0,
+                         unsigned key1, const float* sigma, cudaStream_t st);
 
 }  // namespace mppi

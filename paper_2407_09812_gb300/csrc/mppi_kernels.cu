@@ -64,16 +64,37 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint4* rk) {
     return c;
 }
 
-// Uniform in (0, 1) from the top 23 bits: (2m + 1) 2^-24, exact in FP32.
+// Uniform in (0, 1) from the top 23 bits m: (2m + 1) 2^-24, exact in FP32.
+// Formed as (1 + m 2^-23) - (1 - 2^-24): the first operand is m placed in
+// the mantissa of 1.0, both operands and the difference are FP32 numbers,
+// so the subtraction is exact (no integer-to-float conversion).
 __device__ __forceinline__ float uniform01(unsigned r) {
-    return __uint2float_rn(((r >> 9) << 1) | 1u) * 5.9604644775390625e-08f;
+    return __uint_as_float(0x3f800000u | (r >> 9)) - 0.99999994039535522f;
+}
+
+// -2 ln u for u of the map above, u in [2^-24, 1 - 2^-24].  Away from 1 it
+// is -2 ln 2 log2(u) with the hardware log2 (lg2.approx: absolute error
+// about 2^-22 for u in [0.5, 1), a few ulp below); for d = 1 - u <= 2^-6
+// (d exact there), where an absolute error in log2 would dominate the small
+// result, it is the Mercator series -2 ln(1 - d) = 2 (d + d^2/2 + d^3/3 +
+// d^4/4 + ...) to the fourth term, whose truncation is below d^4/5 <= 2^-24
+// relative.  Measured over all 2^23 values of the map: relative error of
+// -2 ln u at most 2.4e-6 and of its square root (the Box-Muller radius) at
+// most 1.3e-6, absolute 7.2e-7 (the square root by x rsqrt(x)).
+__device__ __forceinline__ float neg2log(float u) {
+    float l;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(u));
+    const float far = -1.3862943611198906f * l;
+    const float d = 1.0f - u;
+    const float near = d * fmaf(d, fmaf(d, fmaf(d, 0.5f, 0.66666669f), 1.0f), 2.0f);
+    return d <= 0.015625f ? near : far;
 }
 
 // Box-Muller on the two uniform pairs of one Philox output.
 __device__ __forceinline__ float4 box_muller4(const uint4 r) {
     const float u0 = uniform01(r.x), u1 = uniform01(r.y), u2 = uniform01(r.z), u3 = uniform01(r.w);
-    // -2 ln u > 0 for every u of the map (u < 1), so sqrt(x) = x rsqrt(x).
-    const float a01 = -2.0f * logf(u0), a23 = -2.0f * logf(u2);
+    // neg2log > 0 over the whole map (u < 1), so sqrt(x) = x rsqrt(x).
+    const float a01 = neg2log(u0), a23 = neg2log(u2);
     const float rad01 = a01 * rsqrtf(a01);
     const float rad23 = a23 * rsqrtf(a23);
     // Angle 2 pi u taken as 2 pi u - pi in (-pi, pi), where the hardware
@@ -1563,6 +1584,38 @@ int max_active_blocks(Shape s, size_t smem) {
         case 32: return occupancy_t<32, 0>(s.block, smem);
         default: return 1;
     }
+}
+
+// The sampling step alone: delta for samples k0 .. k0 + K - 1, steps
+// 0 .. N - 1, element e = (k - k0) N + j, by the device functions the
+// rollouts call (same counters, keys and rounding, so the same bits).
+__global__ void __launch_bounds__(256) noise_kernel(float4* out, unsigned k0, int K, int N,
+                                                    unsigned long long iter, unsigned key0, unsigned key1,
+                                                    float4 sig) {
+    uint4 rk[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) rk[i] = philox_round_keys(key0, key1, (unsigned)i);
+    const uint2 pt = philox_pre_tile(iter, rk);
+    const float sigma[4] = {sig.x, sig.y, sig.z, sig.w};
+    const long long total = (long long)K * N;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const long long kk = e / N;
+        const unsigned j = (unsigned)(e - kk * N);
+        const PhiloxPre pp = philox_pre_sample(k0 + (unsigned)kk, iter, rk);
+        out[e] = noise_delta(normals4_pre(j, pp, &pt, rk), sigma);
+    }
+}
+
+cudaError_t launch_noise(float* out, unsigned k0, int K, int N, unsigned long long iter, unsigned key0,
+                         unsigned key1, const float* sigma, cudaStream_t st) {
+    const long long total = (long long)K * N;
+    const long long blocks = (total + 255) / 256;
+    const long long cap = 8ll * sm_count();
+    const int grid = (int)(blocks < cap ? blocks : cap);
+    noise_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<float4*>(out), k0, K, N, iter, key0, key1,
+                                       make_float4(sigma[0], sigma[1], sigma[2], sigma[3]));
+    return cudaGetLastError();
 }
 
 int sm_count() {

@@ -118,6 +118,7 @@ def lib():
     L.mppi_solve_batch_graph.argtypes = [_VP, C.POINTER(Instance), C.c_int32, _VP]
     L.mppi_solve_batch_host.argtypes = [_VP, _VP, C.c_int32]
     L.mppi_measure_peaks.argtypes = [C.POINTER(Peaks), _VP]
+    L.mppi_sample_noise.argtypes = [C.POINTER(Params), C.c_uint64, C.c_uint32, C.c_int32, C.c_int32, _VP, _VP]
     L.mppi_set_shape.argtypes = [_VP, C.POINTER(Shape)]
     L.mppi_get_shape.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape)]
     L.mppi_autotune.argtypes = [_VP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Shape), _VP]
@@ -517,6 +518,22 @@ def measure_peaks(stream=None) -> dict:
     p = Peaks()
     _check(lib().mppi_measure_peaks(C.byref(p), _stream_ptr(stream)), "mppi_measure_peaks")
     return {f: getattr(p, f) for f, _ in Peaks._fields_ if f != "reserved"}
+
+
+def sample_noise(params: dict, it: int, k0: int, K: int, N: int, out=None, stream=None):
+    """mppi_sample_noise: the noise delta u_{k,j} (Sec. III-A) that a solve
+    with these parameters at iteration `it` draws, for samples k0 .. k0+K-1
+    and steps 0 .. N-1, into `out` (a contiguous CUDA float32 tensor of shape
+    (K, N, 4); allocated when None).  Returns `out`."""
+    import torch
+    if out is None:
+        out = torch.empty((K, N, 4), dtype=torch.float32, device="cuda")
+    if out.numel() < 4 * K * N:
+        raise ValueError("out holds fewer than K*N*4 floats")
+    P = make_params(params)
+    _check(lib().mppi_sample_noise(C.byref(P), int(it), int(k0), int(K), int(N), _dptr(out), _stream_ptr(stream)),
+           "mppi_sample_noise")
+    return out
 
 
 def version() -> str:

@@ -207,3 +207,22 @@ def test_noalloc_refuses_misaligned_and_oversized_arguments_on_the_host(built):
     for K, N in ((32769, 10), (256, 257)):
         pp = mppi.make_params(I.params(K=K, N=N))
         assert call(pp=pp) == mppi.EINVAL, (K, N)
+
+
+def test_sample_noise_refuses_bad_arguments_on_the_host(built):
+    """mppi_sample_noise validates before any launch: NULL or misaligned
+    output, invalid params, K or N out of range and a sample range past
+    2^32 return MPPI_EINVAL (the address is never dereferenced)."""
+    from paper_2407_09812_gb300 import inputs as I
+    from paper_2407_09812_gb300 import mppi
+    L = mppi.lib()
+    p = mppi.make_params(I.params(K=256, N=10))
+    out = 0x7f0000000000
+    assert L.mppi_sample_noise(C.byref(p), 0, 0, 4, 4, None, None) == mppi.EINVAL
+    assert L.mppi_sample_noise(None, 0, 0, 4, 4, out, None) == mppi.EINVAL
+    assert L.mppi_sample_noise(C.byref(p), 0, 0, 4, 4, out + 4, None) == mppi.EINVAL
+    for K, N in ((0, 4), (4, 0), (mppi.K_MAX + 1, 1), (4, mppi.N_MAX + 1)):
+        assert L.mppi_sample_noise(C.byref(p), 0, 0, K, N, out, None) == mppi.EINVAL, (K, N)
+    assert L.mppi_sample_noise(C.byref(p), 0, (1 << 32) - 3, 4, 1, out, None) == mppi.EINVAL
+    bad = mppi.make_params(I.params(sigma=(1.0, float("nan"), 1.0, 1.0)))
+    assert L.mppi_sample_noise(C.byref(bad), 0, 0, 4, 4, out, None) == mppi.EINVAL
