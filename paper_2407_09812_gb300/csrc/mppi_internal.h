@@ -124,8 +124,8 @@ struct LaunchArgs {
 
 constexpr unsigned ERR_TIMEOUT = 1u;
 
-// Floats of one tile partial: rho_t (FP64, two slots), eta_t, the merge scale
-// s_t, then Sigma_t[N][4].
+// Floats of one tile partial: rho_t (a cost pair hi, lo), eta_t, the merge
+// scale s_t, then Sigma_t[N][4].
 MPPI_HD inline int partial_stride(int N) { return 4 + 4 * N; }
 
 // Host-side validation and conversion of the public parameter structs.

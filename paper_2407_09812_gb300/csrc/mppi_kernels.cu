@@ -780,10 +780,63 @@ __device__ __forceinline__ float warp_min(float v) {
     return v;
 }
 
-__device__ __forceinline__ double warp_min_d(double v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
-    return v;
+// ------------------------------------------------------------ cost pairs
+
+// Weight below which exp(-x) is zero in FP32 (denormals included): such
+// samples contribute exactly nothing and are skipped.
+constexpr float kMaxExpArg = 104.0f;
+
+// A rollout cost S_k = c_obs (states in collision) + (S - Sc), the
+// compensated sum of the continuous terms, is carried as an unevaluated
+// pair of floats (hi, lo) with hi + lo equal to it to about 2^-44 relative:
+// the product c_obs n by its FMA-exact error, the additions by TwoSum
+// (Knuth), and hi the FP32 rounding of the sum (|lo| <= ulp(hi) / 2).  The
+// minimum, the differences S_k - rho and the softmin arguments are then
+// formed in FP32 arithmetic with a resolution far below the FP32 rounding
+// of the cost itself, so the large collision term does not swamp the
+// differences the weights depend on; nothing runs on the FP64 pipe, which
+// on this GPU issues a small fraction of the FP32 rate.  The intrinsics keep
+// the compiler from fusing the product into a later addition.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+__device__ __forceinline__ float2 cost_pair(float c_obs, int nhit, float S, float Sc) {
+    const float n = (float)nhit;  // exact (nhit <= N)
+    const float p = __fmul_rn(c_obs, n);
+    const float pe = fmaf(c_obs, n, -p);  // c_obs n = p + pe exactly
+    const float2 h = two_sum(p, S);       // p + S = h.x + h.y exactly
+    return two_sum(h.x, __fadd_rn(h.y, __fsub_rn(pe, Sc)));
+}
+
+// Order-preserving 64-bit key of a pair (hi, lo): lexicographic in hi, then
+// lo, which orders pairs by value.
+__device__ __forceinline__ unsigned long long pair_key(float2 v) {
+    return ((unsigned long long)float_key(v.x) << 32) | float_key(v.y);
+}
+
+__device__ __forceinline__ float2 key_pair(unsigned long long k) {
+    return make_float2(key_float((unsigned)(k >> 32)), key_float((unsigned)k));
+}
+
+// Smallest key of the warp, by two 32-bit hardware reductions.
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long k) {
+    const unsigned hi = (unsigned)(k >> 32);
+    const unsigned mh = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_min_sync(0xffffffffu, hi == mh ? (unsigned)k : 0xffffffffu);
+    return ((unsigned long long)mh << 32) | ml;
+}
+
+// Softmin weight exp(-(v - rho) / lambda) of a cost pair v >= rho (Eq.
+// cost_2 after the minimum shift); exactly 0 for a non-finite cost and below
+// the FP32 range.
+__device__ __forceinline__ float softmin_weight(float2 v, float2 rho, float lambda) {
+    if (!(v.x < INFINITY)) return 0.0f;
+    const float dv = __fadd_rn(__fsub_rn(v.x, rho.x), __fsub_rn(v.y, rho.y));
+    const float xarg = dv / lambda;
+    return xarg <= kMaxExpArg ? expf(-xarg) : 0.0f;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -832,10 +885,6 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     return L;
 }
 
-// Weight below which exp(-x) is zero in FP32 (denormals included): such
-// samples contribute exactly nothing and are skipped.
-constexpr float kMaxExpArg = 104.0f;
-
 // --------------------------------------------------------------- the kernel
 
 // MINB > 1: an instantiation for blocks of at most 128 threads compiled to
@@ -847,10 +896,10 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ DevInstance sI;
     __shared__ int s_tile, s_inst, s_tile_in_inst, s_last, s_count, s_abort, s_lost;
-    __shared__ float s_x0[16], s_xhat[13], s_eta;
-    __shared__ double s_rho;
-    __shared__ double s_redd[32];
-    __shared__ float s_red[32];
+    __shared__ float s_x0[16], s_xhat[13];
+    __shared__ unsigned long long s_wkey[16];  // per-warp minimum cost key
+    __shared__ int s_wcnt[16];                 // per-warp contributor count
+    __shared__ float s_red[16];                // per-warp weight sum
     __shared__ uint4 s_rk[5];  // Philox round keys of the tile's instance
     __shared__ uint2 s_pt;     // the first round's per-tile words
 
@@ -868,7 +917,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
     float4* sobs = reinterpret_cast<float4*>(smem + L.obs);
     float4* sref = reinterpret_cast<float4*>(smem + L.ref);
     float4* su = reinterpret_cast<float4*>(smem + L.u);
-    double* sS = reinterpret_cast<double*>(smem + L.S);
+    float2* sS = reinterpret_cast<float2*>(smem + L.S);  // cost pairs (hi, lo)
     float* sE = reinterpret_cast<float*>(smem + L.e);
     int* slist = reinterpret_cast<int*>(smem + L.list);
     float4* spart = reinterpret_cast<float4*>(smem + L.part);
@@ -1009,7 +1058,7 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
 
             // S_k = c_obs * (states in collision) + the continuous cost, kept
             // apart: the indicator is an exact count and the continuous part a
-            // compensated FP32 sum, combined in FP64 only for the weights.
+            // compensated FP32 sum, combined into a float pair (cost_pair).
             Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float S = 0.0f, Sc = 0.0f;
             int nhit = 0;
@@ -1045,9 +1094,9 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 if (wlane == 0 && kept) atomicAdd(a.stats, (unsigned long long)kept * nvalid);
             }
             if (lane == 0) {
-                const double Sd = (double)C.c_obs * (double)nhit + ((double)S - (double)Sc);
-                if (valid && sI.costs) sI.costs[k_raw] = (float)Sd;
-                sS[group] = (valid && isfinite(Sd)) ? Sd : (double)INFINITY;
+                const float2 Sk = cost_pair(C.c_obs, nhit, S, Sc);
+                if (valid && sI.costs) sI.costs[k_raw] = Sk.x;
+                sS[group] = (valid && isfinite(Sk.x)) ? Sk : make_float2(INFINITY, 0.0f);
             }
             __syncthreads();
         } else {
@@ -1213,9 +1262,9 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                     if (wlane == 0 && kept) atomicAdd(a.stats, (unsigned long long)kept * nvalid);
                 }
                 if (lane == 0) {  // the cost lanes of a sample hold bitwise identical sums
-                    const double Sd = (double)C.c_obs * (double)nhit + ((double)S - (double)Sc);
-                    if (valid && sI.costs) sI.costs[k_raw] = (float)Sd;
-                    sS[group] = (valid && isfinite(Sd)) ? Sd : (double)INFINITY;
+                    const float2 Sk = cost_pair(C.c_obs, nhit, S, Sc);
+                    if (valid && sI.costs) sI.costs[k_raw] = Sk.x;
+                    sS[group] = (valid && isfinite(Sk.x)) ? Sk : make_float2(INFINITY, 0.0f);
                 }
             }
             g_run += (unsigned)N;
@@ -1224,43 +1273,50 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
         }
 
         // ------------------------------------- tile min, weights, eta_t
-        if (warp == 0) {
-            double m = INFINITY;
-            for (int g = wlane; g < spb; g += 32) m = fmin(m, sS[g]);
-            m = warp_min_d(m);
-            if (wlane == 0) s_rho = m;
+        // Sample g's cost is handled by thread g (spb <= nthreads), in the
+        // first nsw warps.  rho_t: each of those warps reduces its 32 keys,
+        // every thread takes the minimum of the warp minima.  Then each
+        // sample's weight; per warp the contributors (weight > 0) by ballot
+        // and the weight sum by a fixed shuffle tree; eta_t and the ascending
+        // contributor list from the per-warp results in warp order.
+        const int nsw = (spb + 31) >> 5;
+        if (warp < nsw) {
+            const unsigned long long kk = tid < spb ? pair_key(sS[tid]) : ~0ull;
+            const unsigned long long m = warp_min_key(kk);
+            if (wlane == 0) s_wkey[warp] = m;
         }
         __syncthreads();
-        const double rho_t = s_rho;
-        for (int g = tid; g < spb; g += nthreads) {
-            const double sv = sS[g];
-            const float xarg = (float)((sv - rho_t) / (double)lambda);
-            sE[g] = (sv < INFINITY && xarg <= kMaxExpArg) ? expf(-xarg) : 0.0f;
-        }
-        __syncthreads();
-        // eta_t in a fixed order and the ascending list of contributors.
-        if (warp == 0) {
-            float acc = 0.0f;
-            for (int g = wlane; g < spb; g += 32) acc += sE[g];
-            acc = warp_sum(acc);
-            int base = 0;
-            for (int c0 = 0; c0 < spb; c0 += 32) {
-                const int g = c0 + wlane;
-                const bool on = g < spb && sE[g] > 0.0f;
-                const unsigned bal = __ballot_sync(0xffffffffu, on);
-                if (on) slist[base + __popc(bal & ((1u << wlane) - 1u))] = g;
-                base += __popc(bal);
+        unsigned long long mk = s_wkey[0];
+        for (int w = 1; w < nsw; ++w) mk = min(mk, s_wkey[w]);
+        const float2 rho_t = key_pair(mk);
+        float e_own = 0.0f;
+        unsigned rank = 0;
+        if (warp < nsw) {
+            if (tid < spb) {
+                e_own = softmin_weight(sS[tid], rho_t, lambda);
+                sE[tid] = e_own;
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, e_own > 0.0f);
+            rank = __popc(bal & ((1u << wlane) - 1u));
+            const float ws = warp_sum(e_own);
             if (wlane == 0) {
-                s_eta = acc;
-                s_count = base;
+                s_wcnt[warp] = __popc(bal);
+                s_red[warp] = ws;
             }
         }
+        __syncthreads();
+        float eta_t = 0.0f;
+        int count = 0, list_at = 0;
+        for (int w = 0; w < nsw; ++w) {
+            if (w == warp) list_at = count;
+            eta_t += s_red[w];
+            count += s_wcnt[w];
+        }
+        if (e_own > 0.0f) slist[list_at + (int)rank] = tid;
         __syncthreads();
 
         // ---------------------- weighted sum of the regenerated noise
         // Threads (j, grp): grp-th share of the contributors for step j.
-        const int count = s_count;
         {
             const int G = N >= nthreads ? 1 : nthreads / N;
             const int tile_base = tile * spb;
@@ -1289,8 +1345,9 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 reinterpret_cast<float4*>(P + 4)[j] = s;
             }
             if (tid == 0) {
-                *reinterpret_cast<double*>(P) = rho_t;
-                P[2] = s_eta;
+                P[0] = rho_t.x;
+                P[1] = rho_t.y;
+                P[2] = eta_t;
                 P[3] = 0.0f;
             }
         }
@@ -1312,52 +1369,42 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             // (rho_t, eta_t) is read once into shared memory and the merge
             // scales s_t stay there; otherwise they go through the partials.
             const bool fast = T <= spb;
-            // rho = min rho_t (FP64 header of each partial)
-            double m = INFINITY;
+            // rho = min rho_t (the cost-pair header of each partial): per
+            // thread, per warp by key, then every thread over the warps.
+            unsigned long long mk = ~0ull;
             for (int t = tid; t < T; t += nthreads) {
-                const double rt = __ldcg(reinterpret_cast<const double*>(P0 + (long long)t * stride));
+                const float2 rt = __ldcg(reinterpret_cast<const float2*>(P0 + (long long)t * stride));
                 if (fast) {
                     sS[t] = rt;
                     sE[t] = __ldcg(P0 + (long long)t * stride + 2);
                 }
-                m = fmin(m, rt);
+                mk = min(mk, pair_key(rt));
             }
-            m = warp_min_d(m);
-            if (wlane == 0) s_redd[warp] = m;
+            mk = warp_min_key(mk);
+            if (wlane == 0) s_wkey[warp] = mk;
             __syncthreads();
-            if (warp == 0) {
-                double v = wlane < nwarps ? s_redd[wlane] : (double)INFINITY;
-                v = warp_min_d(v);
-                if (wlane == 0) s_rho = v;
-            }
-            __syncthreads();
-            const double rho = s_rho;
+            mk = s_wkey[0];
+            for (int w = 1; w < nwarps; ++w) mk = min(mk, s_wkey[w]);
+            const float2 rho = key_pair(mk);
             // s_t = exp(-(rho_t - rho)/lambda), kept in shared memory (fast)
-            // or in the partial's pad slot; eta = sum_t s_t eta_t.
+            // or in the partial's pad slot; eta = sum_t s_t eta_t (per warp
+            // by a shuffle tree, then over the warps in order).
             float* Pw = a.partials + sI.part_off;
             float eacc = 0.0f;
             for (int t = tid; t < T; t += nthreads) {
-                const double rt =
-                    fast ? sS[t] : __ldcg(reinterpret_cast<const double*>(P0 + (long long)t * stride));
+                const float2 rt = fast ? sS[t] : __ldcg(reinterpret_cast<const float2*>(P0 + (long long)t * stride));
                 const float et = fast ? sE[t] : __ldcg(P0 + (long long)t * stride + 2);
-                const float xarg = (float)((rt - rho) / (double)lambda);
-                const float st = (rt < INFINITY && xarg <= kMaxExpArg) ? expf(-xarg) : 0.0f;
+                const float st = softmin_weight(rt, rho, lambda);
                 if (fast) sE[t] = st;
                 else __stcg(Pw + (long long)t * stride + 3, st);
                 eacc = fmaf(st, et, eacc);
             }
             eacc = warp_sum(eacc);
-            __syncthreads();
             if (wlane == 0) s_red[warp] = eacc;
             __syncthreads();
-            if (warp == 0) {
-                float v = wlane < nwarps ? s_red[wlane] : 0.0f;
-                v = warp_sum(v);
-                if (wlane == 0) s_eta = v;
-            }
-            __syncthreads();
-            const float eta = s_eta;
-            const bool ok = rho < INFINITY && eta > 0.0f;
+            float eta = 0.0f;
+            for (int w = 0; w < nwarps; ++w) eta += s_red[w];
+            const bool ok = rho.x < INFINITY && eta > 0.0f;
             const unsigned errs = a.errflags[inst];
             // u_out = u_nom + Sigma / eta   (Eq. u_update), Sigma = sum_t
             // s_t Sigma_t.  The tiles with s_t > 0 are compacted, in
