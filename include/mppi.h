@@ -312,7 +312,15 @@ typedef struct {
                                samples per block); 2: in addition a noise
                                thread per sample in its own warp that draws
                                the noise ahead of the dynamics thread
-                               (block / (2 + lanes) samples per block)      */
+                               (block / (2 + lanes) samples per block); 3:
+                               in addition the dynamics split over two
+                               threads in separate warps, one for the
+                               constraint pipeline and the attitude part of
+                               RK4, one for velocity, position and the
+                               tracking cost, the noise thread forming the
+                               clamped control (block / (3 + lanes)
+                               samples per block); the per-sample costs of
+                               forms 1-3 are bitwise equal                  */
     float list_margin;      /* obstacle tiling: a warp's kept-obstacle list
                                covers the box of its positions grown by
                                this many metres and is reused while they

@@ -457,7 +457,9 @@ int persistent_grid(Shape s, size_t smem) { return sm_count() * max_active_block
 
 // Candidate launch shapes of the autotuners: one thread or 2/4/8/32 lanes
 // per sample (blocks 64-512, at least 8 samples per block), and the
-// pipelined form with one or two cost lanes per sample.
+// pipelined forms (dynamics thread; with a noise thread; with a noise thread
+// and the dynamics split into attitude and translation threads) with one or
+// two cost lanes per sample.
 static std::vector<Shape> tuning_candidates() {
     std::vector<Shape> cands;
     for (int b : {64, 128, 256, 512})
@@ -467,6 +469,8 @@ static std::vector<Shape> tuning_candidates() {
     for (int b : {192, 384}) cands.push_back(Shape{b, 2, 1, 0.0f});
     for (int b : {192, 384}) cands.push_back(Shape{b, 1, 2, 0.0f});
     for (int b : {256, 512}) cands.push_back(Shape{b, 2, 2, 0.0f});
+    for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 3, 0.0f});
+    cands.push_back(Shape{320, 2, 3, 0.0f});
     return cands;
 }
 

@@ -188,34 +188,36 @@ __device__ __forceinline__ void comp_add2(float& x0, float& x1, float& c0, float
     c0 = c.x; c1 = c.y;
 }
 
-// Eq. drone_dynamics with collective thrust over mass Fm and torque over
-// inertia (tJx, tJy, tJz) held constant over the step.
-__device__ __forceinline__ void deriv(const DevModel& M, const State& s, float Fm, float tJx, float tJy, float tJz,
-                                      State& d) {
-    d.px = s.vx;
-    d.py = s.vy;
-    d.pz = s.vz;
+// Eq. drone_dynamics split by what each part depends on: the attitude
+// and body rates (q, omega) evolve on their own, given the torque over inertia
+// (tJx, tJy, tJz); the acceleration depends on the attitude alone, given the
+// collective thrust over mass Fm; p_dot = v.  Every operation is written out
+// (fmaf, __fmul_rn), so the compiler contracts nothing and each part rounds
+// identically wherever it is inlined (one thread, or the two warps of the
+// split pipelined form).
+struct Att {
+    float qw, qx, qy, qz, wx, wy, wz;
+};
+
+__device__ __forceinline__ Att att_deriv(const DevModel& M, const Att& s, float tJx, float tJy, float tJz) {
+    Att d;
     const float hx = 0.5f * s.wx, hy = 0.5f * s.wy, hz = 0.5f * s.wz;
-    d.qw = -s.qx * hx - s.qy * hy - s.qz * hz;
-    d.qx = s.qw * hx + s.qy * hz - s.qz * hy;
-    d.qy = s.qw * hy - s.qx * hz + s.qz * hx;
-    d.qz = s.qw * hz + s.qx * hy - s.qy * hx;
-    // Thrust along the body z axis, R(q) e_z (F/m), then gravity.
-    const float F2 = 2.0f * Fm;
-    d.vx = (s.qx * s.qz + s.qw * s.qy) * F2;
-    d.vy = (s.qy * s.qz - s.qw * s.qx) * F2;
-    d.vz = fmaf(-F2, s.qx * s.qx + s.qy * s.qy, Fm - M.g);
-    d.wx = tJx - M.kx * s.wy * s.wz;
-    d.wy = tJy - M.ky * s.wz * s.wx;
-    d.wz = tJz - M.kz * s.wx * s.wy;
+    d.qw = fmaf(-s.qz, hz, fmaf(-s.qy, hy, __fmul_rn(-s.qx, hx)));
+    d.qx = fmaf(-s.qz, hy, fmaf(s.qy, hz, __fmul_rn(s.qw, hx)));
+    d.qy = fmaf(s.qz, hx, fmaf(-s.qx, hz, __fmul_rn(s.qw, hy)));
+    d.qz = fmaf(-s.qy, hx, fmaf(s.qx, hy, __fmul_rn(s.qw, hz)));
+    d.wx = fmaf(-__fmul_rn(M.kx, s.wy), s.wz, tJx);
+    d.wy = fmaf(-__fmul_rn(M.ky, s.wz), s.wx, tJy);
+    d.wz = fmaf(-__fmul_rn(M.kz, s.wx), s.wy, tJz);
+    return d;
 }
 
-__device__ __forceinline__ void axpy(State& o, const State& x, float h, const State& k) {
-    o.px = fmaf(h, k.px, x.px); o.py = fmaf(h, k.py, x.py); o.pz = fmaf(h, k.pz, x.pz);
-    o.qw = fmaf(h, k.qw, x.qw); o.qx = fmaf(h, k.qx, x.qx); o.qy = fmaf(h, k.qy, x.qy);
-    o.qz = fmaf(h, k.qz, x.qz);
-    o.vx = fmaf(h, k.vx, x.vx); o.vy = fmaf(h, k.vy, x.vy); o.vz = fmaf(h, k.vz, x.vz);
-    o.wx = fmaf(h, k.wx, x.wx); o.wy = fmaf(h, k.wy, x.wy); o.wz = fmaf(h, k.wz, x.wz);
+// Thrust along the body z axis, R(q) e_z (F/m), then gravity.
+__device__ __forceinline__ float3 accel(const DevModel& M, float4 q, float Fm) {
+    const float F2 = 2.0f * Fm;
+    return make_float3(__fmul_rn(fmaf(q.y, q.w, __fmul_rn(q.x, q.z)), F2),
+                       __fmul_rn(fmaf(q.z, q.w, -__fmul_rn(q.x, q.y)), F2),
+                       fmaf(-F2, fmaf(q.y, q.y, __fmul_rn(q.z, q.z)), Fm - M.g));
 }
 
 // Low-order parts of position and velocity (compensated summation).
@@ -223,87 +225,101 @@ struct Comp {
     float px, py, pz, vx, vy, vz;
 };
 
-__device__ __forceinline__ void comp_add(float& x, float& c, float inc) {
-    const float y = inc - c;
-    const float t = x + y;
-    c = (t - x) - y;
-    x = t;
-}
+// Attitudes (w, x, y, z) at which RK4's second, third and fourth stages are
+// evaluated.
+struct Stages {
+    float4 q1, q2, q3;
+};
 
-__device__ __forceinline__ void axpy_inc(State& o, float h, const State& k) {
-    o.px = fmaf(h, k.px, o.px); o.py = fmaf(h, k.py, o.py); o.pz = fmaf(h, k.pz, o.pz);
-    o.qw = fmaf(h, k.qw, o.qw); o.qx = fmaf(h, k.qx, o.qx); o.qy = fmaf(h, k.qy, o.qy);
-    o.qz = fmaf(h, k.qz, o.qz);
-    o.vx = fmaf(h, k.vx, o.vx); o.vy = fmaf(h, k.vy, o.vy); o.vz = fmaf(h, k.vz, o.vz);
-    o.wx = fmaf(h, k.wx, o.wx); o.wy = fmaf(h, k.wy, o.wy); o.wz = fmaf(h, k.wz, o.wz);
-}
-
-// Classical RK4 step of length h, inputs held, then q renormalised.  The
-// four stage increments are summed first and added to the state once;
-// position and velocity carry a compensation term across steps so that
-// their FP32 rounding does not accumulate over the horizon.  Since p_dot = v
-// and v_dot does not depend on p or v, the position increment of the four
-// stages is h v_0 + h^2/6 (a_1 + a_2 + a_3), a_i the stages' accelerations
-// (the classical combination written out), so the stages' velocities are
-// not formed.
-__device__ __forceinline__ void rk4(const DevModel& M, State& x, Comp& c, float Fm, float tJx, float tJy, float tJz,
-                                    float h) {
-    const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f), hh6 = h * h6;
-    State k, xs, inc;
-    deriv(M, x, Fm, tJx, tJy, tJz, k);
-    float ax = k.vx, ay = k.vy, az = k.vz;
-    // Attitude, rates and velocity increments in pairs (packed FP32x2).
+// Classical RK4 step of length h, inputs held, for the attitude and rates:
+// the four stage increments are summed first and added once, then q is
+// renormalised.  Returns the stage attitudes the translation part needs.
+__device__ __forceinline__ Stages rk4_att(const DevModel& M, State& x, float tJx, float tJy, float tJz, float h) {
+    const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
+    const Att x0 = {x.qw, x.qx, x.qy, x.qz, x.wx, x.wy, x.wz};
+    Att k = att_deriv(M, x0, tJx, tJy, tJz);
     float2 i_q0 = __fmul2_rn(f2(h6, h6), f2(k.qw, k.qx)), i_q1 = __fmul2_rn(f2(h6, h6), f2(k.qy, k.qz));
-    float2 i_w = __fmul2_rn(f2(h6, h6), f2(k.wx, k.wy)), i_v = __fmul2_rn(f2(h6, h6), f2(k.vx, k.vy));
-    float i_wz = h6 * k.wz, i_vz = h6 * k.vz;
-    const float2 x_q0 = f2(x.qw, x.qx), x_q1 = f2(x.qy, x.qz), x_w = f2(x.wx, x.wy);
-    auto stage = [&](float hs) {  // xs = x + hs k (attitude and rates; the rest is not used)
+    float2 i_w = __fmul2_rn(f2(h6, h6), f2(k.wx, k.wy));
+    float i_wz = h6 * k.wz;
+    const float2 x_q0 = f2(x0.qw, x0.qx), x_q1 = f2(x0.qy, x0.qz), x_w = f2(x0.wx, x0.wy);
+    Att xs;
+    auto stage = [&](float hs) {  // xs = x + hs k
         const float2 H = f2(hs, hs);
         const float2 q0 = __ffma2_rn(H, f2(k.qw, k.qx), x_q0), q1 = __ffma2_rn(H, f2(k.qy, k.qz), x_q1);
         const float2 w = __ffma2_rn(H, f2(k.wx, k.wy), x_w);
         xs.qw = q0.x; xs.qx = q0.y; xs.qy = q1.x; xs.qz = q1.y;
-        xs.wx = w.x; xs.wy = w.y; xs.wz = fmaf(hs, k.wz, x.wz);
-        xs.vx = x.vx; xs.vy = x.vy; xs.vz = x.vz;
-        xs.px = x.px; xs.py = x.py; xs.pz = x.pz;
+        xs.wx = w.x; xs.wy = w.y; xs.wz = fmaf(hs, k.wz, x0.wz);
+        return make_float4(xs.qw, xs.qx, xs.qy, xs.qz);
     };
     auto add = [&](float hc) {
         const float2 H = f2(hc, hc);
         i_q0 = __ffma2_rn(H, f2(k.qw, k.qx), i_q0);
         i_q1 = __ffma2_rn(H, f2(k.qy, k.qz), i_q1);
         i_w = __ffma2_rn(H, f2(k.wx, k.wy), i_w);
-        i_v = __ffma2_rn(H, f2(k.vx, k.vy), i_v);
         i_wz = fmaf(hc, k.wz, i_wz);
-        i_vz = fmaf(hc, k.vz, i_vz);
     };
-    stage(h2);
-    deriv(M, xs, Fm, tJx, tJy, tJz, k);
+    Stages st;
+    st.q1 = stage(h2);
+    k = att_deriv(M, xs, tJx, tJy, tJz);
     add(h3);
-    ax += k.vx; ay += k.vy; az += k.vz;
-    stage(h2);
-    deriv(M, xs, Fm, tJx, tJy, tJz, k);
+    st.q2 = stage(h2);
+    k = att_deriv(M, xs, tJx, tJy, tJz);
     add(h3);
-    ax += k.vx; ay += k.vy; az += k.vz;
-    stage(h);
-    deriv(M, xs, Fm, tJx, tJy, tJz, k);
+    st.q3 = stage(h);
+    k = att_deriv(M, xs, tJx, tJy, tJz);
     add(h6);
-    inc.qw = i_q0.x; inc.qx = i_q0.y; inc.qy = i_q1.x; inc.qz = i_q1.y;
-    inc.wx = i_w.x; inc.wy = i_w.y; inc.wz = i_wz;
-    inc.vx = i_v.x; inc.vy = i_v.y; inc.vz = i_vz;
-    inc.px = fmaf(h, x.vx, hh6 * ax);
-    inc.py = fmaf(h, x.vy, hh6 * ay);
-    inc.pz = fmaf(h, x.vz, hh6 * az);
-    comp_add2(x.px, x.py, c.px, c.py, inc.px, inc.py);
-    comp_add2(x.vx, x.vy, c.vx, c.vy, inc.vx, inc.vy);
-    comp_add2(x.pz, x.vz, c.pz, c.vz, inc.pz, inc.vz);
-    float2 q0 = __fadd2_rn(f2(x.qw, x.qx), f2(inc.qw, inc.qx));
-    float2 q1 = __fadd2_rn(f2(x.qy, x.qz), f2(inc.qy, inc.qz));
-    const float2 w = __fadd2_rn(f2(x.wx, x.wy), f2(inc.wx, inc.wy));
-    x.wx = w.x; x.wy = w.y; x.wz += inc.wz;
+    float2 q0 = __fadd2_rn(x_q0, i_q0);
+    float2 q1 = __fadd2_rn(x_q1, i_q1);
+    const float2 w = __fadd2_rn(x_w, i_w);
+    x.wx = w.x; x.wy = w.y; x.wz += i_wz;
     const float2 n2 = __ffma2_rn(q1, q1, __fmul2_rn(q0, q0));
     const float n = rsqrtf(n2.x + n2.y);
     q0 = __fmul2_rn(q0, f2(n, n));
     q1 = __fmul2_rn(q1, f2(n, n));
     x.qw = q0.x; x.qx = q0.y; x.qy = q1.x; x.qz = q1.y;
+    return st;
+}
+
+// Translation part of the same RK4 step: v_dot depends on the attitude only
+// and p_dot = v, so the position increment of the four stages is
+// h v_0 + h^2/6 (a_1 + a_2 + a_3), a_i the stages' accelerations (the
+// classical combination written out), and the velocity increment the
+// classical weighted sum of a_1..a_4.  q0 is the attitude at the step's start.
+// Position and velocity carry a compensation term across steps so that
+// their FP32 rounding does not accumulate over the horizon.
+__device__ __forceinline__ void rk4_trans(const DevModel& M, State& x, Comp& c, float4 q0, const Stages& st, float Fm,
+                                          float h) {
+    const float h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f), hh6 = h * h6;
+    float3 a = accel(M, q0, Fm);
+    float ax = a.x, ay = a.y, az = a.z;
+    float2 i_v = __fmul2_rn(f2(h6, h6), f2(a.x, a.y));
+    float i_vz = h6 * a.z;
+    auto add = [&](float hc) {
+        i_v = __ffma2_rn(f2(hc, hc), f2(a.x, a.y), i_v);
+        i_vz = fmaf(hc, a.z, i_vz);
+    };
+    a = accel(M, st.q1, Fm);
+    add(h3);
+    ax += a.x; ay += a.y; az += a.z;
+    a = accel(M, st.q2, Fm);
+    add(h3);
+    ax += a.x; ay += a.y; az += a.z;
+    a = accel(M, st.q3, Fm);
+    add(h6);
+    const float ipx = fmaf(h, x.vx, hh6 * ax);
+    const float ipy = fmaf(h, x.vy, hh6 * ay);
+    const float ipz = fmaf(h, x.vz, hh6 * az);
+    comp_add2(x.px, x.py, c.px, c.py, ipx, ipy);
+    comp_add2(x.vx, x.vy, c.vx, c.vy, i_v.x, i_v.y);
+    comp_add2(x.pz, x.vz, c.pz, c.vz, ipz, i_vz);
+}
+
+// One whole RK4 step (both parts).
+__device__ __forceinline__ void rk4(const DevModel& M, State& x, Comp& c, float Fm, float tJx, float tJy, float tJz,
+                                    float h) {
+    const float4 q0 = make_float4(x.qw, x.qx, x.qy, x.qz);
+    const Stages st = rk4_att(M, x, tJx, tJy, tJz, h);
+    rk4_trans(M, x, c, q0, st, Fm, h);
 }
 
 // Uncompensated step (single use: prediction, plant step).
@@ -846,20 +862,25 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Dynamic shared memory layout (byte offsets), identical on host and device.
-// The pipelined variant adds, per pair of (dynamics, cost) warps, a ring of
-// kRing slots (kSlotF4 float4 per lane, stored lane-contiguous: the position
-// and the step's tracking cost, the position's compensation terms, and the
-// control) and four mbarriers per slot: [2] / [3] full / empty of that ring,
+// The pipelined variant adds, per group of 32 samples, a ring of kRing
+// slots (kSlotF4 float4 per lane, stored lane-contiguous: the position and
+// the step's tracking cost, the position's compensation terms, and the
+// control) from the warp that integrates the position to the cost lanes,
+// and kBarsPerSlot mbarriers per slot: [2] / [3] full / empty of that ring,
 // [0] / [1] full / empty of the noise ring (one float4 per lane and slot)
-// that the noise warp of the PIPE == 2 form fills.
+// that the noise warp of the PIPE >= 2 forms fills, [4] / [5] full / empty
+// of the attitude ring (kAttF4 float4 per lane and slot) from the attitude
+// warp to the translation warp of the PIPE == 3 form.
 constexpr int kRing = 4;
 constexpr int kSlotF4 = 3;
+constexpr int kAttF4 = 6;
+__host__ __device__ constexpr int bars_per_slot(int pipe) { return pipe == 3 ? 6 : 4; }
 // States the cost lanes of the pipelined form score per pass over their
 // kept-obstacle list (at most kRing).
 constexpr int kStatesPerPass = 2;
 
 struct SmemLayout {
-    unsigned obs, ref, u, S, e, list, part, wlist, xring, nring, bars, total;
+    unsigned obs, ref, u, S, e, list, part, wlist, xring, nring, qring, bars, total;
 };
 
 __host__ __device__ inline unsigned align_up(unsigned v, unsigned a) { return (v + a - 1) / a * a; }
@@ -879,8 +900,9 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
     L.part = o; o = align_up(o + 16u * (unsigned)npart, 128);
     L.wlist = o; o = align_up(o + 48u * (unsigned)block, 128);  // 96 float4 (32 obstacle pairs) per warp
     L.xring = o; o = align_up(o + 16u * kSlotF4 * slots, 128);
-    L.nring = o; o = align_up(o + (pipe == 2 ? 16u * slots : 0u), 128);
-    L.bars = o;  o = align_up(o + 8u * 4u * (slots / 32u), 128);
+    L.nring = o; o = align_up(o + (pipe >= 2 ? 16u * slots : 0u), 128);
+    L.qring = o; o = align_up(o + (pipe == 3 ? 16u * kAttF4 * slots : 0u), 128);
+    L.bars = o;  o = align_up(o + 8u * (unsigned)bars_per_slot(pipe) * (slots / 32u), 128);
     L.total = o;
     return L;
 }
@@ -907,7 +929,9 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
     const int nthreads = blockDim.x;
     // PIPE 1: samples [0, spb) have a dynamics thread (tid < spb) and LANES
     // cost lanes (tid >= spb) in separate warps; PIPE 2: also a noise thread
-    // (spb <= tid < 2 spb); otherwise LANES lanes per sample.
+    // (spb <= tid < 2 spb); PIPE 3: the dynamics split over an attitude
+    // thread (tid < spb) and a translation thread (2 spb <= tid < 3 spb),
+    // with the noise thread in between; otherwise LANES lanes per sample.
     const int spb = PIPE ? nthreads / (PIPE + LANES) : nthreads / LANES;
     const int group = PIPE ? (tid < PIPE * spb ? tid % spb : (tid - PIPE * spb) / LANES) : tid / LANES;
     const int lane = PIPE ? (tid < PIPE * spb ? 0 : (tid - PIPE * spb) % LANES) : tid % LANES;
@@ -929,9 +953,9 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
         mbar_init(bar, 1);
         s_abort = 0;
         s_lost = 0;
-        if (PIPE)  // per (pair, slot): [2] state full (dynamics warp), [3] state empty (cost lanes)
-            for (int b = 0; b < (spb / 32) * kRing * 4; ++b)
-                mbar_init(smem_addr(smem + L.bars) + 8u * b, (b & 3) == 3 ? 32 * LANES : 32);
+        if (PIPE)  // per (group, slot): [3] state empty (cost lanes) counts 32 LANES arrivals, the others 32
+            for (int b = 0; b < (spb / 32) * kRing * bars_per_slot(PIPE); ++b)
+                mbar_init(smem_addr(smem + L.bars) + 8u * b, b % bars_per_slot(PIPE) == 3 ? 32 * LANES : 32);
     }
     __syncthreads();
     unsigned g_run = 0;  // pipeline steps run so far by this block (ring slot / phase)
@@ -1110,15 +1134,24 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             // memory.  The cost lanes add the input and input-change cost and
             // score the positions, two states per pass, against the obstacles
             // and the grid while the dynamics thread is already integrating
-            // the next steps.  Every wait is bounded.
+            // the next steps.  With PIPE == 3 the noise thread also forms the
+            // clamped control, and the dynamics are split: the attitude
+            // thread runs the constraint pipeline and the attitude part of
+            // RK4 and hands the stage attitudes, the new attitude and rates
+            // and F/m to the translation thread, which integrates velocity
+            // and position, forms the tracking cost and feeds the cost lanes.
+            // Every wait is bounded.
             const bool is_cost = tid >= PIPE * spb;
-            const bool is_noise = PIPE == 2 && tid >= spb && !is_cost;
+            const bool is_noise = PIPE >= 2 && tid >= spb && tid < 2 * spb;
+            const bool is_trans = PIPE == 3 && tid >= 2 * spb && !is_cost;
             const int pw = group >> 5;  // warp pair
             float4* xring = reinterpret_cast<float4*>(smem + L.xring);
             const unsigned bars = smem_addr(smem + L.bars);
             volatile int* abort_flag = &s_abort;
             auto slot_of = [&](unsigned g) { return (int)(g % kRing); };
-            auto bar_of = [&](int slot, int kind) { return bars + 8u * (unsigned)((pw * kRing + slot) * 4 + kind); };
+            auto bar_of = [&](int slot, int kind) {
+                return bars + 8u * (unsigned)((pw * kRing + slot) * bars_per_slot(PIPE) + kind);
+            };
             // Field f of this lane's entry in a ring slot.
             auto ring_at = [&](int slot, int f) { return xring + ((pw * kRing + slot) * kSlotF4 + f) * 32 + (group & 31); };
             constexpr int X_FULL = 2, X_EMPTY = 3;
@@ -1126,6 +1159,12 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             float4* nring = reinterpret_cast<float4*>(smem + L.nring);
             auto nring_at = [&](int slot) { return nring + (pw * kRing + slot) * 32 + (group & 31); };
             constexpr int N_FULL = 0, N_EMPTY = 1;
+            // Attitude ring (PIPE == 3): field f of this lane's entry.
+            float4* qring = reinterpret_cast<float4*>(smem + L.qring);
+            auto qring_at = [&](int slot, int f) {
+                return qring + ((pw * kRing + slot) * kAttF4 + f) * 32 + (group & 31);
+            };
+            constexpr int Q_FULL = 4, Q_EMPTY = 5;
             const int k_raw = tile * spb + group;
             const bool valid = k_raw < K;
             const unsigned k = (unsigned)(valid ? k_raw : K - 1);
@@ -1135,17 +1174,67 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
             x.wx = s_x0[10]; x.wy = s_x0[11]; x.wz = s_x0[12];
             Comp cmp = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (is_noise) {
-                // Noise thread (PIPE == 2): draws delta for every step ahead of
-                // the dynamics thread and hands it over through its own ring.
+                // Noise thread (PIPE >= 2): draws delta for every step ahead of
+                // the dynamics and hands it over through its own ring (PIPE ==
+                // 3: the clamped control u_nom_j + delta instead).
                 const PhiloxPre ppre = philox_pre_sample(k, iter, s_rk);
                 for (int j = 0; j < N; ++j) {
                     const unsigned g = g_run + (unsigned)j;
                     const int slot = slot_of(g);
                     const unsigned ph = (g / kRing) & 1u;
-                    const float4 d = noise_delta(normals4_pre((unsigned)j, ppre, &s_pt, s_rk), sigma);
+                    float4 d = noise_delta(normals4_pre((unsigned)j, ppre, &s_pt, s_rk), sigma);
+                    if (PIPE == 3) d = clamp_input(Mdl, perturb(su[j], d));
                     if (g >= (unsigned)kRing) mbar_wait_or_abort(bar_of(slot, N_EMPTY), ph ^ 1u, abort_flag, wait_polls);
                     *nring_at(slot) = d;
                     mbar_arrive(bar_of(slot, N_FULL));
+                }
+            } else if (PIPE == 3 && !is_cost && !is_trans) {
+                // Attitude thread: control from the noise ring, constraint
+                // pipeline, attitude part of RK4.
+                for (int j = 0; j < N; ++j) {
+                    const unsigned g = g_run + (unsigned)j;
+                    const int slot = slot_of(g);
+                    const unsigned ph = (g / kRing) & 1u;
+                    mbar_wait_or_abort(bar_of(slot, N_FULL), ph, abort_flag, wait_polls);
+                    const float4 u = *nring_at(slot);
+                    mbar_arrive(bar_of(slot, N_EMPTY));
+                    const Feasible f = feasible(Mdl, x, u, inv_dt);
+                    const Stages st = rk4_att(Mdl, x, f.tJx, f.tJy, f.tJz, dt);
+                    if (g >= (unsigned)kRing) mbar_wait_or_abort(bar_of(slot, Q_EMPTY), ph ^ 1u, abort_flag, wait_polls);
+                    *qring_at(slot, 0) = st.q1;
+                    *qring_at(slot, 1) = st.q2;
+                    *qring_at(slot, 2) = st.q3;
+                    *qring_at(slot, 3) = make_float4(x.qw, x.qx, x.qy, x.qz);
+                    *qring_at(slot, 4) = make_float4(x.wx, x.wy, x.wz, f.Fm);
+                    *qring_at(slot, 5) = u;
+                    mbar_arrive(bar_of(slot, Q_FULL));
+                }
+            } else if (is_trans) {
+                // Translation thread: velocity and position from the stage
+                // attitudes, the step's input, input-change and tracking cost
+                // (in the one-thread form's order), hand-over to the cost lanes.
+                float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int j = 0; j < N; ++j) {
+                    const unsigned g = g_run + (unsigned)j;
+                    const int slot = slot_of(g);
+                    const unsigned ph = (g / kRing) & 1u;
+                    mbar_wait_or_abort(bar_of(slot, Q_FULL), ph, abort_flag, wait_polls);
+                    Stages st;
+                    st.q1 = *qring_at(slot, 0);
+                    st.q2 = *qring_at(slot, 1);
+                    st.q3 = *qring_at(slot, 2);
+                    const float4 qn = *qring_at(slot, 3), wf = *qring_at(slot, 4), u = *qring_at(slot, 5);
+                    mbar_arrive(bar_of(slot, Q_EMPTY));
+                    rk4_trans(Mdl, x, cmp, make_float4(x.qw, x.qx, x.qy, x.qz), st, wf.w, dt);
+                    x.qw = qn.x; x.qx = qn.y; x.qy = qn.z; x.qz = qn.w;
+                    x.wx = wf.x; x.wy = wf.y; x.wz = wf.z;
+                    float scost = input_cost(C, u, u_prev, j > 0);
+                    u_prev = u;
+                    scost += tracking_cost(C, x, cmp, &sref[4 * (j + 1)]);
+                    if (g >= (unsigned)kRing) mbar_wait_or_abort(bar_of(slot, X_EMPTY), ph ^ 1u, abort_flag, wait_polls);
+                    *ring_at(slot, 0) = make_float4(x.px, x.py, x.pz, scost);
+                    *ring_at(slot, 1) = make_float4(cmp.px, cmp.py, cmp.pz, 0.0f);
+                    mbar_arrive(bar_of(slot, X_FULL));
                 }
             } else if (!is_cost) {
                 const PhiloxPre ppre = philox_pre_sample(k, iter, s_rk);
@@ -1196,10 +1285,16 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 // order.
                 float4 u_prev = make_float4(0.f, 0.f, 0.f, 0.f);
                 auto take = [&](int sl, int jj, float& qpx, float& qpy, float& qpz) -> float {
-                    const float4 r0 = *ring_at(sl, 0), r1 = *ring_at(sl, 1), u = *ring_at(sl, 2);
-                    float c = input_cost(C, u, u_prev, jj > 0);
-                    u_prev = u;
-                    c += r0.w;
+                    const float4 r0 = *ring_at(sl, 0), r1 = *ring_at(sl, 1);
+                    float c;
+                    if (PIPE == 3) {
+                        c = r0.w;  // input, input-change and tracking cost, formed by the translation thread
+                    } else {
+                        const float4 u = *ring_at(sl, 2);
+                        c = input_cost(C, u, u_prev, jj > 0);
+                        u_prev = u;
+                        c += r0.w;
+                    }
                     qpx = r0.x - r1.x;
                     qpy = r0.y - r1.y;
                     qpz = r0.z - r1.z;
@@ -1464,9 +1559,13 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                     }
                 }
                 const float acc[4] = {sg.x, sg.y, sg.z, sg.w};
+                // u_nom_j as staged in shared memory (sunew aliases it; this
+                // thread reads its row before it overwrites it).
+                const float4 un4 = su[j];
+                const float unj[4] = {un4.x, un4.y, un4.z, un4.w};
                 for (int c = 0; c < 4; ++c) {
                     const int o = 4 * j + c;
-                    const float un = sI.u_nom[o];
+                    const float un = unj[c];
                     const float v = ok ? un + acc[c] / eta : un;
                     sunew[o] = v;
                     if (sI.u_out) sI.u_out[o] = v;
@@ -1528,9 +1627,10 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
 constexpr int kMinBlocks128 = 6;
 
 bool shape_supported(Shape s) {
-    if (s.pipe == 1 || s.pipe == 2) {
-        // A dynamics warp (and with pipe 2 a noise warp) plus `lanes` cost
-        // warps per 32 samples.
+    if (s.pipe >= 1 && s.pipe <= 3) {
+        // A dynamics warp (pipe 2: and a noise warp; pipe 3: an attitude, a
+        // noise and a translation warp) plus `lanes` cost warps per 32
+        // samples.
         const int unit = 32 * (s.pipe + s.lanes);
         return (s.lanes == 1 || s.lanes == 2) && s.block >= unit && s.block <= 512 && s.block % unit == 0;
     }
@@ -1596,6 +1696,11 @@ cudaError_t launch_tiles(const LaunchArgs& args, Shape s, int grid, size_t smem,
         if (s.lanes == 2) return launch_t<2, 2>(a, s.block, grid, smem, st);
         return cudaErrorInvalidValue;
     }
+    if (s.pipe == 3) {
+        if (s.lanes == 1) return launch_t<1, 3>(a, s.block, grid, smem, st);
+        if (s.lanes == 2) return launch_t<2, 3>(a, s.block, grid, smem, st);
+        return cudaErrorInvalidValue;
+    }
     switch (s.lanes) {
         case 1:
             return s.block <= 128 ? launch_t<1, 0, kMinBlocks128>(a, s.block, grid, smem, st)
@@ -1621,6 +1726,7 @@ static int occupancy_t(int block, size_t smem) {
 int max_active_blocks(Shape s, size_t smem) {
     if (s.pipe == 1) return s.lanes == 2 ? occupancy_t<2, 1>(s.block, smem) : occupancy_t<1, 1>(s.block, smem);
     if (s.pipe == 2) return s.lanes == 2 ? occupancy_t<2, 2>(s.block, smem) : occupancy_t<1, 2>(s.block, smem);
+    if (s.pipe == 3) return s.lanes == 2 ? occupancy_t<2, 3>(s.block, smem) : occupancy_t<1, 3>(s.block, smem);
     switch (s.lanes) {
         case 1:
             return s.block <= 128 ? occupancy_t<1, 0, kMinBlocks128>(s.block, smem)

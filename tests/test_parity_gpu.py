@@ -134,6 +134,7 @@ def test_every_launch_shape_matches_and_is_deterministic(M, orc, inp):
     shapes += [(128, 1, 1, 0.0), (256, 1, 1, 0.0), (512, 1, 1, 0.0), (96, 2, 1, 0.0), (192, 2, 1, 0.0),
                (384, 2, 1, 0.0)]
     shapes += [(96, 1, 2, 0.0), (192, 1, 2, 0.0), (384, 1, 2, 0.0), (256, 2, 2, 0.0), (512, 2, 2, 0.0)]
+    shapes += [(128, 1, 3, 0.0), (256, 1, 3, 0.0), (512, 1, 3, 0.0), (160, 2, 3, 0.0), (480, 2, 3, 0.0)]
     shapes += [(128, 1, 0, 0.25), (128, 4, 0, 3.0), (256, 1, 1, 2.0), (256, 32, 0, 0.5)]
     for shape in shapes:
         a = gpu_solve(M, prob, shape=shape)
@@ -154,7 +155,7 @@ def test_pipelined_form_matches_one_thread_per_sample(M, orc, inp, K, N, Mo):
         prob["obstacles"] = np.zeros((0, 4), np.float32)
     b = gpu_solve(M, prob, shape=(128, 1, 0))
     ref = orc.mppi_step(prob, n_threads=16)
-    for shape in ((256, 1, 1), (384, 2, 1), (384, 1, 2), (512, 2, 2)):
+    for shape in ((256, 1, 1), (384, 2, 1), (384, 1, 2), (512, 2, 2), (512, 1, 3), (320, 2, 3)):
         a = gpu_solve(M, prob, shape=shape)
         assert cost_err(a["costs"], b["costs"])[0] <= 1e-6
         assert_step_close(prob, a, ref)
@@ -169,6 +170,13 @@ def test_pipelined_form_matches_one_thread_per_sample(M, orc, inp, K, N, Mo):
     sig = prob["params"]["sigma"]
     for k in ("u_out", "u_next", "u_cmd"):
         assert control_err(three[k], two[k], sig) <= 1e-6, k
+    # The split form (pipelined = 3: attitude and translation threads, the
+    # noise thread forming the clamped control) runs the same operations on
+    # other threads: per-sample costs bitwise those of the forms above.
+    four = gpu_solve(M, prob, shape=(512, 1, 3))
+    assert np.array_equal(four["costs"], two["costs"])
+    for k in ("u_out", "u_next", "u_cmd"):
+        assert control_err(four[k], two[k], sig) <= 1e-6, k
 
 
 def test_closed_loop_full_size(M, orc, inp):
