@@ -207,7 +207,8 @@ def mufu_ops(rollout_steps: float, pairs: float) -> dict:
 
 
 def shape_dict(s) -> dict:
-    return {"block": s[0], "lanes": s[1], "pipelined": s[2], "list_margin": s[3]}
+    return {"block": s[0], "lanes": s[1], "pipelined": s[2], "list_margin": s[3],
+            "samples_per_thread": s[4] if len(s) > 4 else 1}
 
 
 def flusher():
@@ -916,7 +917,7 @@ def main():
     ap.add_argument("--serve-vehicles", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="only the headline fleet and its end-to-end figure")
     ap.add_argument("--no-oracle", action="store_true", help="skip the stress workload's FP64 oracle comparison")
-    ap.add_argument("--shape", default="", help="fleet launch shape 'block,lanes,pipelined,margin' instead of the "
+    ap.add_argument("--shape", default="", help="launch shape 'block,lanes,pipelined,margin[,samples_per_thread]' instead of the "
                                                 "batch autotuner's (profiling aid)")
     ap.add_argument("--section", default="all",
                     choices=["all", "fleet", "closed_loop", "stress", "serving", "paper", "options", "plain"],

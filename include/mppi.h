@@ -327,6 +327,13 @@ typedef struct {
                                stay inside (0: the default, 1 m, or 0.5 m
                                for the pipelined form; results do not
                                depend on it beyond FP32 rounding)           */
+    int32_t samples_per_thread; /* 1 (0 reads as 1), or 2 with pipelined 0,
+                               lanes 1 and blocks of 64 or 128 threads:
+                               each thread rolls out samples tid and
+                               block + tid of its tile, the arithmetic
+                               packed across the two (FP32x2); per-sample
+                               results equal those of one sample per
+                               thread to FP32 rounding                      */
 } mppi_shape;
 
 /* Forces a launch shape for subsequent calls on the handle (both 0: back

@@ -132,9 +132,14 @@ Shape default_shape(long long K, int N, int M) {
     // Fewer 128-sample tiles than SMs and a real obstacle set: the step is
     // bound by each warp's dependent chain, and the pipelined form (a
     // dynamics and a cost thread per sample, separate warps) overlaps the
-    // obstacle scoring with the integration; otherwise one thread per
-    // sample.  The autotuner refines per size bucket.
-    if ((K + 127) / 128 < (long long)mppi::sm_count() && M >= 16) return Shape{256, 1, 1};
+    // obstacle scoring with the integration.  Enough samples for a
+    // 256-sample tile on every SM: the launch is bound by issue rate, and two
+    // samples per thread (packed arithmetic) issue fewer instructions;
+    // otherwise one thread per sample.  The autotuner refines per size
+    // bucket.
+    const long long sms = (long long)mppi::sm_count();
+    if ((K + 127) / 128 < sms && M >= 16) return Shape{256, 1, 1};
+    if ((K + 255) / 256 >= sms) return Shape{128, 1, 0, 0.0f, 2};
     return Shape{128, 1, 0};
 }
 
@@ -297,7 +302,7 @@ DevInstance make_instance(const mppi_ctx* h, const mppi_instance& in, Shape s) {
     d.iter_dev = reinterpret_cast<unsigned long long*>(in.iter_dev);
     d.iter = in.iter;
     d.K = in.K; d.N = in.N; d.M = in.M;
-    const int spb = s.pipe ? s.block / (s.pipe + s.lanes) : s.block / s.lanes;
+    const int spb = samples_per_block(s);
     d.n_tiles = (in.K + spb - 1) / spb;
     d.dt = in.dt; d.lambda = in.lambda;
     for (int c = 0; c < 4; ++c) d.sigma[c] = in.sigma[c];
@@ -384,7 +389,7 @@ int plan_batch(mppi_ctx* h, const mppi_instance* ins, int n, BatchPlan* plan) {
         Mmax = std::max(Mmax, ins[i].M);
     }
     Shape s = choose_shape(h, sumK / n, Nmax, Mmax, sumK);
-    const int spb = s.pipe ? s.block / (s.pipe + s.lanes) : s.block / s.lanes;
+    const int spb = samples_per_block(s);
     long long tiles = 0;
     size_t pf = 0;
     for (int i = 0; i < n; ++i) {
@@ -471,6 +476,7 @@ static std::vector<Shape> tuning_candidates() {
     for (int b : {256, 512}) cands.push_back(Shape{b, 2, 2, 0.0f});
     for (int b : {128, 256, 512}) cands.push_back(Shape{b, 1, 3, 0.0f});
     cands.push_back(Shape{320, 2, 3, 0.0f});
+    for (int b : {64, 128}) cands.push_back(Shape{b, 1, 0, 0.0f, 2});
     return cands;
 }
 
@@ -547,6 +553,7 @@ static int tune_on(mppi_ctx* h, mppi_instance in, cudaStream_t st, mppi_shape* b
         best->lanes = bestS.lanes;
         best->pipelined = bestS.pipe;
         best->list_margin = list_margin(bestS);
+        best->samples_per_thread = bestS.spt;
     }
     return MPPI_OK;
 }
@@ -718,7 +725,9 @@ int mppi_set_shape(mppi_handle h, const mppi_shape* shape) {
         return MPPI_OK;
     }
     if (!(shape->list_margin >= 0.0f && shape->list_margin <= 1e3f)) return MPPI_EINVAL;
-    Shape s{shape->block, shape->lanes, shape->pipelined, shape->list_margin};
+    if (shape->samples_per_thread < 0 || shape->samples_per_thread > 2) return MPPI_EINVAL;
+    Shape s{shape->block, shape->lanes, shape->pipelined, shape->list_margin,
+            shape->samples_per_thread ? shape->samples_per_thread : 1};
     if (!shape_supported(s)) return MPPI_EINVAL;
     h->forced = s;
     return MPPI_OK;
@@ -731,6 +740,7 @@ int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* s
     shape->lanes = s.lanes;
     shape->pipelined = s.pipe;
     shape->list_margin = list_margin(s);
+    shape->samples_per_thread = s.spt;
     return MPPI_OK;
 }
 
@@ -808,7 +818,8 @@ int mppi_solve(mppi_handle h, const float* x_hat, const float* ref, const float*
     if (rc) return rc;
     const Shape s = choose_shape(h, in.K, in.N, in.M);
     const std::array<long long, 6> key{(long long)K, (long long)N, (long long)M, costs ? 1 : 0,
-                                       ((long long)s.block << 32) | ((long long)s.lanes << 8) | s.pipe,
+                                       ((long long)s.block << 32) | ((long long)s.lanes << 8) |
+                                           ((long long)s.spt << 4) | s.pipe,
                                        (long long)(list_margin(s) * 1e6f)};
     auto enqueue = [&](cudaStream_t q) -> int {
         if (cudaMemcpyAsync(db, hb, in_end * sizeof(float), cudaMemcpyHostToDevice, q) != cudaSuccess)
@@ -899,7 +910,8 @@ int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_
     const size_t smem = smem_bytes(plan.N_b, plan.M_b, plan.s);
     if (smem > 227 * 1024) return MPPI_EINVAL;
     const std::pair<uint64_t, float> key(((uint64_t)plan.s.block << 48) | ((uint64_t)plan.s.lanes << 40) |
-                                             ((uint64_t)plan.s.pipe << 36) | ((uint64_t)plan.N_b << 20) |
+                                             ((uint64_t)plan.s.spt << 38) | ((uint64_t)plan.s.pipe << 36) |
+                                             ((uint64_t)plan.N_b << 20) |
                                              (uint64_t)plan.M_b,
                                          list_margin(plan.s));
     auto it = h->graphs.find(key);
@@ -1167,6 +1179,7 @@ int mppi_autotune_batch(mppi_handle h, const mppi_instance* instances, int32_t n
         best->lanes = bestS.lanes;
         best->pipelined = bestS.pipe;
         best->list_margin = list_margin(bestS);
+        best->samples_per_thread = bestS.spt;
     }
     return MPPI_OK;
 }

@@ -94,9 +94,16 @@ struct DevInstance {
 struct Shape {
     int block;     // threads per block
     int lanes;     // lanes per sample
-    int pipe;      // 1: pipelined (a dynamics thread and cost lanes per sample); 2: also a noise thread
+    int pipe;      // 1: pipelined (a dynamics thread and cost lanes per sample); 2: also a noise thread;
+                   // 3: also the dynamics split into attitude and translation threads
     float margin;  // kept-obstacle list margin [m]; 0: the default of the form
+    int spt = 1;   // samples per thread (2: pipe 0, lanes 1, blocks of 64 or 128 threads)
 };
+
+// Samples a block of this shape rolls out (the tile size).
+inline int samples_per_block(const Shape& s) {
+    return s.pipe ? s.block / (s.pipe + s.lanes) : s.spt * s.block / s.lanes;
+}
 
 inline float list_margin(const Shape& s) {
     return s.margin > 0.0f ? s.margin : s.pipe ? kCullMarginPipelined : kCullMargin;

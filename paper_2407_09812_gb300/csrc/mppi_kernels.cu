@@ -41,6 +41,22 @@ constexpr unsigned kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Packed FP32x2 arithmetic (two lanes' worth of work per instruction, each
+// element rounded as the scalar operation; the assembler may still fuse a
+// packed multiply into a following packed add, explicit rounding mode or
+// not, so a sequence of packed operations is exact to FP32 rounding, not
+// necessarily bitwise equal to the same sequence written with scalar
+// intrinsics).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+
 __device__ __forceinline__ uint4 philox_round(uint4 c, unsigned k0, unsigned k1) {
     const unsigned hi0 = __umulhi(0xD2511F53u, c.x);
     const unsigned lo0 = 0xD2511F53u * c.x;
@@ -166,17 +182,6 @@ __device__ __forceinline__ float4 perturb(const float4 un, const float4 d) {
 struct State {
     float px, py, pz, qw, qx, qy, qz, vx, vy, vz, wx, wy, wz;
 };
-
-// Packed FP32x2 arithmetic (two lanes' worth of work per instruction, each
-// element rounded exactly as the scalar operation).
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
 
 // Compensated addition of inc to (x0, x1) with compensation terms (c0, c1).
 __device__ __forceinline__ void comp_add2(float& x0, float& x1, float& c0, float& c1, float i0, float i1) {
@@ -314,12 +319,71 @@ __device__ __forceinline__ void rk4_trans(const DevModel& M, State& x, Comp& c, 
     comp_add2(x.pz, x.vz, c.pz, c.vz, ipz, i_vz);
 }
 
-// One whole RK4 step (both parts).
+// One whole RK4 step: the operations of rk4_att and rk4_trans, with each
+// stage's acceleration formed as soon as its attitude is (fewer values live
+// at once).
 __device__ __forceinline__ void rk4(const DevModel& M, State& x, Comp& c, float Fm, float tJx, float tJy, float tJz,
                                     float h) {
-    const float4 q0 = make_float4(x.qw, x.qx, x.qy, x.qz);
-    const Stages st = rk4_att(M, x, tJx, tJy, tJz, h);
-    rk4_trans(M, x, c, q0, st, Fm, h);
+    const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f), hh6 = h * h6;
+    const Att x0 = {x.qw, x.qx, x.qy, x.qz, x.wx, x.wy, x.wz};
+    Att k = att_deriv(M, x0, tJx, tJy, tJz);
+    float2 i_q0 = __fmul2_rn(f2(h6, h6), f2(k.qw, k.qx)), i_q1 = __fmul2_rn(f2(h6, h6), f2(k.qy, k.qz));
+    float2 i_w = __fmul2_rn(f2(h6, h6), f2(k.wx, k.wy));
+    float i_wz = h6 * k.wz;
+    const float2 x_q0 = f2(x0.qw, x0.qx), x_q1 = f2(x0.qy, x0.qz), x_w = f2(x0.wx, x0.wy);
+    float3 a = accel(M, make_float4(x0.qw, x0.qx, x0.qy, x0.qz), Fm);
+    float ax = a.x, ay = a.y, az = a.z;
+    float2 i_v = __fmul2_rn(f2(h6, h6), f2(a.x, a.y));
+    float i_vz = h6 * a.z;
+    Att xs;
+    auto stage = [&](float hs) {  // xs = x + hs k; returns the stage attitude
+        const float2 H = f2(hs, hs);
+        const float2 q0 = __ffma2_rn(H, f2(k.qw, k.qx), x_q0), q1 = __ffma2_rn(H, f2(k.qy, k.qz), x_q1);
+        const float2 w = __ffma2_rn(H, f2(k.wx, k.wy), x_w);
+        xs.qw = q0.x; xs.qx = q0.y; xs.qy = q1.x; xs.qz = q1.y;
+        xs.wx = w.x; xs.wy = w.y; xs.wz = fmaf(hs, k.wz, x0.wz);
+        return make_float4(xs.qw, xs.qx, xs.qy, xs.qz);
+    };
+    auto add = [&](float hc) {
+        const float2 H = f2(hc, hc);
+        i_q0 = __ffma2_rn(H, f2(k.qw, k.qx), i_q0);
+        i_q1 = __ffma2_rn(H, f2(k.qy, k.qz), i_q1);
+        i_w = __ffma2_rn(H, f2(k.wx, k.wy), i_w);
+        i_wz = fmaf(hc, k.wz, i_wz);
+    };
+    auto add_v = [&](float hc) {
+        i_v = __ffma2_rn(f2(hc, hc), f2(a.x, a.y), i_v);
+        i_vz = fmaf(hc, a.z, i_vz);
+    };
+    a = accel(M, stage(h2), Fm);
+    add_v(h3);
+    ax += a.x; ay += a.y; az += a.z;
+    k = att_deriv(M, xs, tJx, tJy, tJz);
+    add(h3);
+    a = accel(M, stage(h2), Fm);
+    add_v(h3);
+    ax += a.x; ay += a.y; az += a.z;
+    k = att_deriv(M, xs, tJx, tJy, tJz);
+    add(h3);
+    a = accel(M, stage(h), Fm);
+    add_v(h6);
+    k = att_deriv(M, xs, tJx, tJy, tJz);
+    add(h6);
+    const float ipx = fmaf(h, x.vx, hh6 * ax);
+    const float ipy = fmaf(h, x.vy, hh6 * ay);
+    const float ipz = fmaf(h, x.vz, hh6 * az);
+    comp_add2(x.px, x.py, c.px, c.py, ipx, ipy);
+    comp_add2(x.vx, x.vy, c.vx, c.vy, i_v.x, i_v.y);
+    comp_add2(x.pz, x.vz, c.pz, c.vz, ipz, i_vz);
+    float2 q0 = __fadd2_rn(x_q0, i_q0);
+    float2 q1 = __fadd2_rn(x_q1, i_q1);
+    const float2 w = __fadd2_rn(x_w, i_w);
+    x.wx = w.x; x.wy = w.y; x.wz += i_wz;
+    const float2 n2 = __ffma2_rn(q1, q1, __fmul2_rn(q0, q0));
+    const float n = rsqrtf(n2.x + n2.y);
+    q0 = __fmul2_rn(q0, f2(n, n));
+    q1 = __fmul2_rn(q1, f2(n, n));
+    x.qw = q0.x; x.qx = q0.y; x.qy = q1.x; x.qz = q1.y;
 }
 
 // Uncompensated step (single use: prediction, plant step).
@@ -717,6 +781,233 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
     sum = t;
 }
 
+// ------------------------------------------------- two samples per thread
+
+// The one-sample functions above with every per-sample quantity a float2
+// (sample A in .x, sample B in .y) and every operation the same one per
+// sample: additions, multiplications and FMAs packed across the two samples
+// (FP32x2), minima, maxima, compares and special functions per sample.  The
+// packed arithmetic halves the instruction count of the dynamics and the
+// cost.  Each sample's results equal the one-sample form's to FP32 rounding,
+// not bitwise: the assembler fuses some packed multiply-add pairs that the
+// one-sample code rounds separately.
+__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 clamp2(float2 v, float lo, float hi) {
+    return make_float2(fminf(fmaxf(v.x, lo), hi), fminf(fmaxf(v.y, lo), hi));
+}
+
+struct State2 {
+    float2 px, py, pz, qw, qx, qy, qz, vx, vy, vz, wx, wy, wz;
+};
+struct Comp2 {
+    float2 px, py, pz, vx, vy, vz;
+};
+struct U2 {  // control (F, omega_x, omega_y, omega_z) of the two samples
+    float2 F, wx, wy, wz;
+};
+
+__device__ __forceinline__ U2 clamp_input_x2(const DevModel& M, U2 u) {
+    u.F = clamp2(u.F, M.F_min, M.F_max);
+    u.wx = clamp2(u.wx, -M.w_max[0], M.w_max[0]);
+    u.wy = clamp2(u.wy, -M.w_max[1], M.w_max[1]);
+    u.wz = clamp2(u.wz, -M.w_max[2], M.w_max[2]);
+    return u;
+}
+
+// u_nom_j + sigma o z for the two samples' standard normals zA, zB.
+__device__ __forceinline__ U2 perturb_x2(const float4 un, const float4 zA, const float4 zB, const float* sigma) {
+    U2 u;
+    u.F = add2(bc(un.x), mul2(bc(sigma[0]), f2(zA.x, zB.x)));
+    u.wx = add2(bc(un.y), mul2(bc(sigma[1]), f2(zA.y, zB.y)));
+    u.wy = add2(bc(un.z), mul2(bc(sigma[2]), f2(zA.z, zB.z)));
+    u.wz = add2(bc(un.w), mul2(bc(sigma[3]), f2(zA.w, zB.w)));
+    return u;
+}
+
+__device__ __forceinline__ float2 input_cost_x2(const DevCost& C, const U2& u, const U2& up, bool rate) {
+    const float2 tx = fma2(bc(C.R[2]), mul2(u.wy, u.wy), mul2(bc(C.R[0]), mul2(u.F, u.F)));
+    const float2 ty = fma2(bc(C.R[3]), mul2(u.wz, u.wz), mul2(bc(C.R[1]), mul2(u.wx, u.wx)));
+    float2 c = add2(tx, ty);
+    if (rate) {
+        const float2 e0 = sub2(u.F, up.F), e1 = sub2(u.wx, up.wx), e2 = sub2(u.wy, up.wy), e3 = sub2(u.wz, up.wz);
+        const float2 rx = fma2(bc(C.Rd[2]), mul2(e2, e2), mul2(bc(C.Rd[0]), mul2(e0, e0)));
+        const float2 ry = fma2(bc(C.Rd[3]), mul2(e3, e3), mul2(bc(C.Rd[1]), mul2(e1, e1)));
+        c = add2(c, add2(rx, ry));
+    }
+    return c;
+}
+
+struct Feasible2 {
+    float2 Fm, tJx, tJy, tJz;
+};
+
+__device__ __forceinline__ Feasible2 feasible_x2(const DevModel& M, const State2& s, const U2& u, float inv_dt) {
+    Feasible2 o;
+    const float2 gx = mul2(mul2(bc(M.dJx), s.wy), s.wz);
+    const float2 gy = mul2(mul2(bc(M.dJy), s.wz), s.wx);
+    const float2 gz = mul2(mul2(bc(M.dJz), s.wx), s.wy);
+    const float2 rx = mul2(sub2(u.wx, s.wx), bc(inv_dt));
+    const float2 ry = mul2(sub2(u.wy, s.wy), bc(inv_dt));
+    const float2 rz = mul2(sub2(u.wz, s.wz), bc(inv_dt));
+    if (M.motor_clip) {
+        const float2 tx = fma2(bc(M.Jx), rx, gx), ty = fma2(bc(M.Jy), ry, gy), tz = fma2(bc(M.Jz), rz, gz);
+        const float2 f0 = mul2(bc(0.25f), u.F);
+        const float2 ex = mul2(tx, bc(M.q_a)), ey = mul2(ty, bc(M.q_a)), ez = mul2(tz, bc(M.q_c));
+        const float2 A = sub2(f0, ez), B = add2(f0, ez), P = add2(ex, ey), Q = sub2(ex, ey);
+        const float2 T0 = clamp2(sub2(A, P), M.T_min, M.T_max);
+        const float2 T1 = clamp2(add2(A, P), M.T_min, M.T_max);
+        const float2 T2 = clamp2(add2(B, Q), M.T_min, M.T_max);
+        const float2 T3 = clamp2(sub2(B, Q), M.T_min, M.T_max);
+        const float2 s01 = add2(T0, T1), s23 = add2(T2, T3);
+        const float2 dx = sub2(add2(T1, T2), add2(T0, T3));
+        const float2 dy = sub2(add2(T1, T3), add2(T0, T2));
+        const float2 dz = sub2(s23, s01);
+        o.Fm = mul2(add2(s01, s23), bc(M.inv_mass));
+        o.tJx = mul2(bc(M.a_Jx), dx);
+        o.tJy = mul2(bc(M.a_Jy), dy);
+        o.tJz = mul2(bc(M.c_Jz), dz);
+    } else {
+        o.Fm = mul2(u.F, bc(M.inv_mass));
+        o.tJx = fma2(bc(M.kx), mul2(s.wy, s.wz), rx);
+        o.tJy = fma2(bc(M.ky), mul2(s.wz, s.wx), ry);
+        o.tJz = fma2(bc(M.kz), mul2(s.wx, s.wy), rz);
+    }
+    return o;
+}
+
+struct Att2 {
+    float2 qw, qx, qy, qz, wx, wy, wz;
+};
+
+// att_deriv with -q_i h_j written as q_i (-h_j) and -(k w_i) w_j as
+// (-k w_i) w_j: the same products, so the same roundings.
+__device__ __forceinline__ Att2 att_deriv_x2(const DevModel& M, const Att2& s, const Feasible2& f) {
+    Att2 d;
+    const float2 hx = mul2(bc(0.5f), s.wx), hy = mul2(bc(0.5f), s.wy), hz = mul2(bc(0.5f), s.wz);
+    const float2 nx = mul2(bc(-0.5f), s.wx), ny = mul2(bc(-0.5f), s.wy), nz = mul2(bc(-0.5f), s.wz);
+    d.qw = fma2(s.qz, nz, fma2(s.qy, ny, mul2(s.qx, nx)));
+    d.qx = fma2(s.qz, ny, fma2(s.qy, hz, mul2(s.qw, hx)));
+    d.qy = fma2(s.qz, hx, fma2(s.qx, nz, mul2(s.qw, hy)));
+    d.qz = fma2(s.qy, nx, fma2(s.qx, hy, mul2(s.qw, hz)));
+    d.wx = fma2(mul2(bc(-M.kx), s.wy), s.wz, f.tJx);
+    d.wy = fma2(mul2(bc(-M.ky), s.wz), s.wx, f.tJy);
+    d.wz = fma2(mul2(bc(-M.kz), s.wx), s.wy, f.tJz);
+    return d;
+}
+
+struct Q2 {
+    float2 qw, qx, qy, qz;
+};
+
+__device__ __forceinline__ void accel_x2(const DevModel& M, const Q2& q, float2 Fm, float2& ax, float2& ay,
+                                         float2& az) {
+    const float2 F2 = mul2(bc(2.0f), Fm);
+    ax = mul2(fma2(q.qx, q.qz, mul2(q.qw, q.qy)), F2);
+    ay = mul2(fma2(q.qy, q.qz, mul2(mul2(q.qw, q.qx), bc(-1.0f))), F2);
+    az = fma2(mul2(bc(-2.0f), Fm), fma2(q.qx, q.qx, mul2(q.qy, q.qy)), sub2(Fm, bc(M.g)));
+}
+
+__device__ __forceinline__ void comp_add_x2(float2& x, float2& c, float2 inc) {
+    const float2 y = sub2(inc, c);
+    const float2 t = add2(x, y);
+    c = sub2(sub2(t, x), y);
+    x = t;
+}
+
+// rk4 for the two samples (the operations of rk4, each stage's
+// acceleration formed as soon as its attitude is).
+__device__ __forceinline__ void rk4_x2(const DevModel& M, State2& x, Comp2& c, const Feasible2& f, float h) {
+    const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f), hh6 = h * h6;
+    const Att2 x0 = {x.qw, x.qx, x.qy, x.qz, x.wx, x.wy, x.wz};
+    Att2 k = att_deriv_x2(M, x0, f);
+    const float2 H6 = bc(h6), H3 = bc(h3);
+    float2 iqw = mul2(H6, k.qw), iqx = mul2(H6, k.qx), iqy = mul2(H6, k.qy), iqz = mul2(H6, k.qz);
+    float2 iwx = mul2(H6, k.wx), iwy = mul2(H6, k.wy), iwz = mul2(H6, k.wz);
+    float2 ax, ay, az, bx, by, bz;
+    accel_x2(M, Q2{x0.qw, x0.qx, x0.qy, x0.qz}, f.Fm, ax, ay, az);
+    float2 ivx = mul2(H6, ax), ivy = mul2(H6, ay), ivz = mul2(H6, az);
+    Att2 xs;
+    auto stage = [&](float hs) {
+        const float2 H = bc(hs);
+        xs.qw = fma2(H, k.qw, x0.qw); xs.qx = fma2(H, k.qx, x0.qx);
+        xs.qy = fma2(H, k.qy, x0.qy); xs.qz = fma2(H, k.qz, x0.qz);
+        xs.wx = fma2(H, k.wx, x0.wx); xs.wy = fma2(H, k.wy, x0.wy); xs.wz = fma2(H, k.wz, x0.wz);
+        return Q2{xs.qw, xs.qx, xs.qy, xs.qz};
+    };
+    auto add = [&](float hc) {
+        const float2 H = bc(hc);
+        iqw = fma2(H, k.qw, iqw); iqx = fma2(H, k.qx, iqx); iqy = fma2(H, k.qy, iqy); iqz = fma2(H, k.qz, iqz);
+        iwx = fma2(H, k.wx, iwx); iwy = fma2(H, k.wy, iwy); iwz = fma2(H, k.wz, iwz);
+    };
+    auto add_v = [&](float2 H) {
+        ivx = fma2(H, bx, ivx); ivy = fma2(H, by, ivy); ivz = fma2(H, bz, ivz);
+    };
+    accel_x2(M, stage(h2), f.Fm, bx, by, bz);
+    add_v(H3);
+    ax = add2(ax, bx); ay = add2(ay, by); az = add2(az, bz);
+    k = att_deriv_x2(M, xs, f);
+    add(h3);
+    accel_x2(M, stage(h2), f.Fm, bx, by, bz);
+    add_v(H3);
+    ax = add2(ax, bx); ay = add2(ay, by); az = add2(az, bz);
+    k = att_deriv_x2(M, xs, f);
+    add(h3);
+    accel_x2(M, stage(h), f.Fm, bx, by, bz);
+    add_v(H6);
+    k = att_deriv_x2(M, xs, f);
+    add(h6);
+    const float2 Hh = bc(h), HH6 = bc(hh6);
+    const float2 ipx = fma2(Hh, x.vx, mul2(HH6, ax));
+    const float2 ipy = fma2(Hh, x.vy, mul2(HH6, ay));
+    const float2 ipz = fma2(Hh, x.vz, mul2(HH6, az));
+    comp_add_x2(x.px, c.px, ipx);
+    comp_add_x2(x.py, c.py, ipy);
+    comp_add_x2(x.vx, c.vx, ivx);
+    comp_add_x2(x.vy, c.vy, ivy);
+    comp_add_x2(x.pz, c.pz, ipz);
+    comp_add_x2(x.vz, c.vz, ivz);
+    float2 qw = add2(x0.qw, iqw), qx = add2(x0.qx, iqx), qy = add2(x0.qy, iqy), qz = add2(x0.qz, iqz);
+    x.wx = add2(x0.wx, iwx);
+    x.wy = add2(x0.wy, iwy);
+    x.wz = add2(x.wz, iwz);
+    const float2 ssum = add2(fma2(qy, qy, mul2(qw, qw)), fma2(qz, qz, mul2(qx, qx)));
+    const float2 n = f2(rsqrtf(ssum.x), rsqrtf(ssum.y));
+    x.qw = mul2(qw, n); x.qx = mul2(qx, n); x.qy = mul2(qy, n); x.qz = mul2(qz, n);
+}
+
+__device__ __forceinline__ float2 tracking_cost_x2(const DevCost& C, const State2& x, const Comp2& c,
+                                                   const float4* row) {
+    const float4 r0 = row[0], r1 = row[1], r2 = row[2], r3 = row[3];
+    const float2 dpx = sub2(sub2(x.px, bc(r0.x)), c.px), dpy = sub2(sub2(x.py, bc(r0.y)), c.py);
+    const float2 dvx = sub2(sub2(x.vx, bc(r0.z)), c.vx), dvy = sub2(sub2(x.vy, bc(r0.w)), c.vy);
+    const float2 dpz = sub2(sub2(x.pz, bc(r1.x)), c.pz), dvz = sub2(sub2(x.vz, bc(r1.y)), c.vz);
+    const float2 dwx = sub2(x.wx, bc(r1.z)), dwy = sub2(x.wy, bc(r1.w)), dwz = sub2(x.wz, bc(r3.x));
+    const float2 qdx = fma2(x.qy, bc(r2.z), mul2(x.qw, bc(r2.x)));
+    const float2 qdy = fma2(x.qz, bc(r2.w), mul2(x.qx, bc(r2.y)));
+    const float2 dot = add2(qdx, qdy);
+    float2 d;
+    if (C.quat_metric == 0) {
+        d = sub2(bc(1.0f), mul2(dot, dot));
+    } else {
+        const float2 t = fma2(mul2(bc(2.0f), dot), dot, bc(-1.0f));
+        d = f2(acosf(fminf(fmaxf(t.x, -1.0f), 1.0f)), acosf(fminf(fmaxf(t.y, -1.0f), 1.0f)));
+    }
+    const float2 ep = add2(add2(mul2(dpx, dpx), mul2(dpy, dpy)), mul2(dpz, dpz));
+    const float2 ev = add2(add2(mul2(dvx, dvx), mul2(dvy, dvy)), mul2(dvz, dvz));
+    const float2 ew = fma2(dwz, dwz, add2(mul2(dwx, dwx), mul2(dwy, dwy)));
+    return fma2(bc(C.c_p), ep, fma2(bc(C.c_q), mul2(d, d), fma2(bc(C.c_v), ev, mul2(bc(C.c_w), ew))));
+}
+
+__device__ __forceinline__ void kahan_add_x2(float2& sum, float2& comp, float2 v) {
+    const float2 y = sub2(v, comp);
+    const float2 t = add2(sum, y);
+    comp = sub2(sub2(t, sum), y);
+    sum = t;
+}
+
 // ------------------------------------------------------------ TMA + mbarrier
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -888,9 +1179,9 @@ struct SmemLayout {
 
 __host__ __device__ inline unsigned align_up(unsigned v, unsigned a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int block, int lanes, int pipe) {
+__host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int block, int lanes, int pipe, int spt) {
     SmemLayout L;
-    const int spb = pipe ? block / (pipe + lanes) : block / lanes;
+    const int spb = pipe ? block / (pipe + lanes) : spt * block / lanes;
     const int npart = block > N_max ? block : N_max;
     const unsigned slots = pipe ? (unsigned)(spb / 32) * kRing * 32u : 0u;
     unsigned o = 0;
@@ -915,16 +1206,16 @@ __host__ __device__ inline SmemLayout smem_layout(int N_max, int M_max, int bloc
 // MINB > 1: an instantiation for blocks of at most 128 threads compiled to
 // fit MINB blocks per SM (a register budget of 65536 / (128 MINB) per
 // thread), for launches that fill the GPU and are bound by issue rate.
-template <int LANES, int PIPE, int MINB>
+template <int LANES, int PIPE, int MINB, int SPT>
 __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(const LaunchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ DevInstance sI;
     __shared__ int s_tile, s_inst, s_tile_in_inst, s_last, s_count, s_abort, s_lost;
     __shared__ float s_x0[16], s_xhat[13];
-    __shared__ unsigned long long s_wkey[16];  // per-warp minimum cost key
-    __shared__ int s_wcnt[16];                 // per-warp contributor count
-    __shared__ float s_red[16];                // per-warp weight sum
+    __shared__ unsigned long long s_wkey[32];  // per-(virtual) warp minimum cost key
+    __shared__ int s_wcnt[32];                 // per-(virtual) warp contributor count
+    __shared__ float s_red[32];                // per-(virtual) warp weight sum
     __shared__ uint4 s_rk[5];  // Philox round keys of the tile's instance
     __shared__ uint2 s_pt;     // the first round's per-tile words
 
@@ -934,13 +1225,14 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
     // cost lanes (tid >= spb) in separate warps; PIPE 2: also a noise thread
     // (spb <= tid < 2 spb); PIPE 3: the dynamics split over an attitude
     // thread (tid < spb) and a translation thread (2 spb <= tid < 3 spb),
-    // with the noise thread in between; otherwise LANES lanes per sample.
-    const int spb = PIPE ? nthreads / (PIPE + LANES) : nthreads / LANES;
+    // with the noise thread in between; otherwise LANES lanes per sample, or
+    // (SPT == 2) two samples per thread, tid and nthreads + tid.
+    const int spb = PIPE ? nthreads / (PIPE + LANES) : SPT * nthreads / LANES;
     const int group = PIPE ? (tid < PIPE * spb ? tid % spb : (tid - PIPE * spb) / LANES) : tid / LANES;
     const int lane = PIPE ? (tid < PIPE * spb ? 0 : (tid - PIPE * spb) % LANES) : tid % LANES;
     const int warp = tid >> 5, wlane = tid & 31, nwarps = nthreads >> 5;
 
-    const SmemLayout L = smem_layout(a.N_max, a.M_max, nthreads, LANES, PIPE);
+    const SmemLayout L = smem_layout(a.N_max, a.M_max, nthreads, LANES, PIPE, SPT);
     float4* sobs = reinterpret_cast<float4*>(smem + L.obs);
     float4* sref = reinterpret_cast<float4*>(smem + L.ref);
     float4* su = reinterpret_cast<float4*>(smem + L.u);
@@ -1074,7 +1366,69 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
         __syncthreads();
 
         // --------------------------------------------------- rollouts
-        if constexpr (PIPE == 0) {
+        if constexpr (PIPE == 0 && SPT == 2) {
+            // Two samples per thread, A (tile sample tid) and B (nthreads +
+            // tid), one thread per sample otherwise: the one-thread form's
+            // arithmetic packed across the two, their positions scored in one
+            // pass over the warp's kept-obstacle list.
+            const int gA = tid, gB = nthreads + tid;
+            const int kA_raw = tile * spb + gA, kB_raw = tile * spb + gB;
+            const bool validA = kA_raw < K, validB = kB_raw < K;
+            const unsigned kA = (unsigned)(validA ? kA_raw : K - 1), kB = (unsigned)(validB ? kB_raw : K - 1);
+            State2 x;
+            x.px = bc(s_x0[0]); x.py = bc(s_x0[1]); x.pz = bc(s_x0[2]); x.qw = bc(s_x0[3]); x.qx = bc(s_x0[4]);
+            x.qy = bc(s_x0[5]); x.qz = bc(s_x0[6]); x.vx = bc(s_x0[7]); x.vy = bc(s_x0[8]); x.vz = bc(s_x0[9]);
+            x.wx = bc(s_x0[10]); x.wy = bc(s_x0[11]); x.wz = bc(s_x0[12]);
+            Comp2 cmp = {bc(0.f), bc(0.f), bc(0.f), bc(0.f), bc(0.f), bc(0.f)};
+            float2 S = bc(0.0f), Sc = bc(0.0f);
+            int nhitA = 0, nhitB = 0;
+            unsigned kept = 0;  // 2 x obstacles evaluated by this warp per position pair
+            WarpList wl;
+            wl.n = -1;
+            float bars[2];
+            bool hits[2];
+            auto score = [&](float2 qx, float2 qy, float2 qz) {
+                const float px[2] = {qx.x, qx.y}, py[2] = {qy.x, qy.y}, pz[2] = {qz.x, qz.y};
+                obstacle_cost_n<1, 2>(C, px, py, pz, sobs, M, lane, wlane, wob, wl, cull_margin, reuse_lists, bars,
+                                      hits, &kept);
+                if (C.grid) {
+                    hits[0] |= grid_hit(C, qx.x + p0x, qy.x + p0y, qz.x + p0z);
+                    hits[1] |= grid_hit(C, qx.y + p0x, qy.y + p0y, qz.y + p0z);
+                }
+                nhitA += hits[0] ? 1 : 0;
+                nhitB += hits[1] ? 1 : 0;
+                return f2(bars[0], bars[1]);
+            };
+            {
+                const float2 tc = tracking_cost_x2(C, x, cmp, &sref[0]);
+                kahan_add_x2(S, Sc, add2(tc, score(x.px, x.py, x.pz)));
+            }
+            U2 u_prev = {bc(0.f), bc(0.f), bc(0.f), bc(0.f)};
+            const PhiloxPre ppA = philox_pre_sample(kA, iter, s_rk), ppB = philox_pre_sample(kB, iter, s_rk);
+            for (int j = 0; j < N; ++j) {
+                const float4 zA = normals4_pre((unsigned)j, ppA, &s_pt, s_rk);
+                const float4 zB = normals4_pre((unsigned)j, ppB, &s_pt, s_rk);
+                const U2 u = clamp_input_x2(Mdl, perturb_x2(su[j], zA, zB, sigma));
+                float2 step = input_cost_x2(C, u, u_prev, j > 0);
+                u_prev = u;
+                const Feasible2 f = feasible_x2(Mdl, x, u, inv_dt);
+                rk4_x2(Mdl, x, cmp, f, dt);
+                step = add2(step, tracking_cost_x2(C, x, cmp, &sref[4 * (j + 1)]));
+                step = add2(step, score(sub2(x.px, cmp.px), sub2(x.py, cmp.py), sub2(x.pz, cmp.pz)));
+                kahan_add_x2(S, Sc, step);
+            }
+            if (a.stats) {
+                const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, validA)) +
+                                        __popc(__ballot_sync(0xffffffffu, validB));
+                if (wlane == 0 && kept) atomicAdd(a.stats, (unsigned long long)(kept / 2) * nvalid);
+            }
+            const float2 SkA = cost_pair(C.c_obs, nhitA, S.x, Sc.x), SkB = cost_pair(C.c_obs, nhitB, S.y, Sc.y);
+            if (validA && sI.costs) sI.costs[kA_raw] = SkA.x;
+            if (validB && sI.costs) sI.costs[kB_raw] = SkB.x;
+            sS[gA] = (validA && isfinite(SkA.x)) ? SkA : make_float2(INFINITY, 0.0f);
+            sS[gB] = (validB && isfinite(SkB.x)) ? SkB : make_float2(INFINITY, 0.0f);
+            __syncthreads();
+        } else if constexpr (PIPE == 0) {
             const int k_raw = tile * spb + group;
             const bool valid = k_raw < K;
             const unsigned k = (unsigned)(valid ? k_raw : K - 1);
@@ -1377,40 +1731,59 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
         // sample's weight; per warp the contributors (weight > 0) by ballot
         // and the weight sum by a fixed shuffle tree; eta_t and the ascending
         // contributor list from the per-warp results in warp order.
+        // With two samples per thread, sample r nthreads + tid belongs to
+        // virtual warp r nwarps + warp (r = 0, 1): the virtual warps are the
+        // samples' 32-aligned groups in ascending order.
         const int nsw = (spb + 31) >> 5;
-        if (warp < nsw) {
-            const unsigned long long kk = tid < spb ? pair_key(sS[tid]) : ~0ull;
-            const unsigned long long m = warp_min_key(kk);
-            if (wlane == 0) s_wkey[warp] = m;
+#pragma unroll
+        for (int r = 0; r < SPT; ++r) {
+            const int vw = r * nwarps + warp, g = r * nthreads + tid;
+            if (vw < nsw) {
+                const unsigned long long kk = g < spb ? pair_key(sS[g]) : ~0ull;
+                const unsigned long long m = warp_min_key(kk);
+                if (wlane == 0) s_wkey[vw] = m;
+            }
         }
         __syncthreads();
         unsigned long long mk = s_wkey[0];
         for (int w = 1; w < nsw; ++w) mk = min(mk, s_wkey[w]);
         const float2 rho_t = key_pair(mk);
-        float e_own = 0.0f;
-        unsigned rank = 0;
-        if (warp < nsw) {
-            if (tid < spb) {
-                e_own = softmin_weight(sS[tid], rho_t, lambda);
-                sE[tid] = e_own;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, e_own > 0.0f);
-            rank = __popc(bal & ((1u << wlane) - 1u));
-            const float ws = warp_sum(e_own);
-            if (wlane == 0) {
-                s_wcnt[warp] = __popc(bal);
-                s_red[warp] = ws;
+        float e_own[SPT];
+        unsigned rank[SPT];
+#pragma unroll
+        for (int r = 0; r < SPT; ++r) {
+            const int vw = r * nwarps + warp, g = r * nthreads + tid;
+            e_own[r] = 0.0f;
+            rank[r] = 0;
+            if (vw < nsw) {
+                if (g < spb) {
+                    e_own[r] = softmin_weight(sS[g], rho_t, lambda);
+                    sE[g] = e_own[r];
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, e_own[r] > 0.0f);
+                rank[r] = __popc(bal & ((1u << wlane) - 1u));
+                const float ws = warp_sum(e_own[r]);
+                if (wlane == 0) {
+                    s_wcnt[vw] = __popc(bal);
+                    s_red[vw] = ws;
+                }
             }
         }
         __syncthreads();
         float eta_t = 0.0f;
-        int count = 0, list_at = 0;
+        int count = 0, list_at[SPT];
+#pragma unroll
+        for (int r = 0; r < SPT; ++r) list_at[r] = 0;
         for (int w = 0; w < nsw; ++w) {
-            if (w == warp) list_at = count;
+#pragma unroll
+            for (int r = 0; r < SPT; ++r)
+                if (w == r * nwarps + warp) list_at[r] = count;
             eta_t += s_red[w];
             count += s_wcnt[w];
         }
-        if (e_own > 0.0f) slist[list_at + (int)rank] = tid;
+#pragma unroll
+        for (int r = 0; r < SPT; ++r)
+            if (e_own[r] > 0.0f) slist[list_at[r] + (int)rank[r]] = r * nthreads + tid;
         __syncthreads();
 
         // ---------------------- weighted sum of the regenerated noise
@@ -1628,8 +2001,13 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
 // warps instead of 16 raise the issue rate of these issue-bound launches
 // (256 uneven instances: 7.52 -> 7.23 ms; at most 85 registers, no spills).
 constexpr int kMinBlocks128 = 6;
+// Two samples per thread (blocks of 64 or 128 threads): compiled for 4
+// blocks of 128 per SM, a budget of 128 registers a thread.
+constexpr int kMinBlocksX2 = 4;
 
 bool shape_supported(Shape s) {
+    if (s.spt == 2) return s.pipe == 0 && s.lanes == 1 && (s.block == 64 || s.block == 128);
+    if (s.spt != 1) return false;
     if (s.pipe >= 1 && s.pipe <= 3) {
         // A dynamics warp (pipe 2: and a noise warp; pipe 3: an attitude, a
         // noise and a translation warp) plus `lanes` cost warps per 32
@@ -1643,7 +2021,7 @@ bool shape_supported(Shape s) {
 }
 
 size_t smem_bytes(int N_max, int M_max, Shape s) {
-    return smem_layout(N_max, M_max, s.block, s.lanes, s.pipe).total;
+    return smem_layout(N_max, M_max, s.block, s.lanes, s.pipe, s.spt).total;
 }
 
 // Largest dynamic shared memory opted in so far, per instantiation and per
@@ -1653,7 +2031,7 @@ size_t smem_bytes(int N_max, int M_max, Shape s) {
 // call.
 constexpr int kMaxDevices = 64;
 
-template <int LANES, int PIPE, int MINB>
+template <int LANES, int PIPE, int MINB, int SPT>
 static std::atomic<int>* smem_opt_in() {
     static std::atomic<int> v[kMaxDevices] = {};
     int dev = 0;
@@ -1664,11 +2042,11 @@ static std::atomic<int>* smem_opt_in() {
     return &v[dev];
 }
 
-template <int LANES, int PIPE, int MINB>
+template <int LANES, int PIPE, int MINB, int SPT>
 static cudaError_t prepare_t(size_t smem) {
-    std::atomic<int>* opt = smem_opt_in<LANES, PIPE, MINB>();
+    std::atomic<int>* opt = smem_opt_in<LANES, PIPE, MINB, SPT>();
     if (opt && (int)smem <= opt->load()) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(mppi_step_kernel<LANES, PIPE, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(mppi_step_kernel<LANES, PIPE, MINB, SPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && opt) {
         int cur = opt->load();
@@ -1678,17 +2056,18 @@ static cudaError_t prepare_t(size_t smem) {
     return e;
 }
 
-template <int LANES, int PIPE, int MINB = 1>
+template <int LANES, int PIPE, int MINB = 1, int SPT = 1>
 static cudaError_t launch_t(const LaunchArgs& a, int block, int grid, size_t smem, cudaStream_t st) {
-    cudaError_t e = prepare_t<LANES, PIPE, MINB>(smem);
+    cudaError_t e = prepare_t<LANES, PIPE, MINB, SPT>(smem);
     if (e != cudaSuccess) return e;
-    mppi_step_kernel<LANES, PIPE, MINB><<<grid, block, smem, st>>>(a);
+    mppi_step_kernel<LANES, PIPE, MINB, SPT><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tiles(const LaunchArgs& args, Shape s, int grid, size_t smem, cudaStream_t st) {
     LaunchArgs a = args;
     a.C.cull_margin = list_margin(s);
+    if (s.spt == 2) return launch_t<1, 0, kMinBlocksX2, 2>(a, s.block, grid, smem, st);
     if (s.pipe == 1) {
         if (s.lanes == 1) return launch_t<1, 1>(a, s.block, grid, smem, st);
         if (s.lanes == 2) return launch_t<2, 1>(a, s.block, grid, smem, st);
@@ -1716,17 +2095,18 @@ cudaError_t launch_tiles(const LaunchArgs& args, Shape s, int grid, size_t smem,
     }
 }
 
-template <int LANES, int PIPE, int MINB = 1>
+template <int LANES, int PIPE, int MINB = 1, int SPT = 1>
 static int occupancy_t(int block, size_t smem) {
     int n = 0;
-    prepare_t<LANES, PIPE, MINB>(smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mppi_step_kernel<LANES, PIPE, MINB>, block, smem) !=
+    prepare_t<LANES, PIPE, MINB, SPT>(smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mppi_step_kernel<LANES, PIPE, MINB, SPT>, block, smem) !=
         cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
 int max_active_blocks(Shape s, size_t smem) {
+    if (s.spt == 2) return occupancy_t<1, 0, kMinBlocksX2, 2>(s.block, smem);
     if (s.pipe == 1) return s.lanes == 2 ? occupancy_t<2, 1>(s.block, smem) : occupancy_t<1, 1>(s.block, smem);
     if (s.pipe == 2) return s.lanes == 2 ? occupancy_t<2, 2>(s.block, smem) : occupancy_t<1, 2>(s.block, smem);
     if (s.pipe == 3) return s.lanes == 2 ? occupancy_t<2, 3>(s.block, smem) : occupancy_t<1, 3>(s.block, smem);

@@ -66,7 +66,8 @@ class Peaks(C.Structure):
 
 
 class Shape(C.Structure):
-    _fields_ = [("block", C.c_int32), ("lanes", C.c_int32), ("pipelined", C.c_int32), ("list_margin", C.c_float)]
+    _fields_ = [("block", C.c_int32), ("lanes", C.c_int32), ("pipelined", C.c_int32), ("list_margin", C.c_float),
+                ("samples_per_thread", C.c_int32)]
 
 
 class ServerCfg(C.Structure):
@@ -428,35 +429,36 @@ class Solver:
         arr = self._instances(instances)
         _check(lib().mppi_autotune_batch(self.h, arr, len(instances), C.byref(s), _stream_ptr(stream)),
                "mppi_autotune_batch")
-        return s.block, s.lanes, s.pipelined, s.list_margin
+        return s.block, s.lanes, s.pipelined, s.list_margin, s.samples_per_thread
 
     def batch_shape(self, instances: list):
-        """(block, lanes, pipelined, list_margin) a batched launch of these
+        """(block, lanes, pipelined, list_margin, samples_per_thread) a batched launch of these
         instances uses."""
         K = sum(int(d["K"]) for d in instances) // len(instances)
         return self.get_shape(K, max(int(d["N"]) for d in instances),
                               max(_obstacle_count(d.get("obstacles")) for d in instances))
 
     # ---------------------------------------------------------- launch shape
-    def set_shape(self, block: int = 0, lanes: int = 0, pipelined: int = 0, list_margin: float = 0.0):
+    def set_shape(self, block: int = 0, lanes: int = 0, pipelined: int = 0, list_margin: float = 0.0,
+                  samples_per_thread: int = 1):
         """mppi_set_shape: force a launch shape (all 0: back to the tuned or
         default choice).  list_margin is the obstacle tiling in metres (0:
-        default)."""
-        s = Shape(block, lanes, pipelined, list_margin)
+        default); samples_per_thread 2 packs two samples per thread."""
+        s = Shape(block, lanes, pipelined, list_margin, samples_per_thread)
         _check(lib().mppi_set_shape(self.h, C.byref(s)), "mppi_set_shape")
 
     def get_shape(self, K: int, N: int, M: int):
-        """(block, lanes, pipelined, list_margin) used for a problem of size (K, N, M)."""
+        """(block, lanes, pipelined, list_margin, samples_per_thread) used for a problem of size (K, N, M)."""
         s = Shape()
         _check(lib().mppi_get_shape(self.h, K, N, M, C.byref(s)), "mppi_get_shape")
-        return s.block, s.lanes, s.pipelined, s.list_margin
+        return s.block, s.lanes, s.pipelined, s.list_margin, s.samples_per_thread
 
     def autotune(self, K: int, N: int, M: int, stream=None):
-        """mppi_autotune: the fastest (block, lanes, pipelined, list_margin)
+        """mppi_autotune: the fastest (block, lanes, pipelined, list_margin, samples_per_thread)
         on a synthetic problem of size (K, N, M)."""
         s = Shape()
         _check(lib().mppi_autotune(self.h, K, N, M, C.byref(s), _stream_ptr(stream)), "mppi_autotune")
-        return s.block, s.lanes, s.pipelined, s.list_margin
+        return s.block, s.lanes, s.pipelined, s.list_margin, s.samples_per_thread
 
     def autotune_on(self, instance: dict, stream=None):
         """mppi_autotune_instance: the fastest shape on one of the caller's
@@ -464,7 +466,7 @@ class Solver:
         s = Shape()
         arr = self._instances([instance])
         _check(lib().mppi_autotune_instance(self.h, arr, C.byref(s), _stream_ptr(stream)), "mppi_autotune_instance")
-        return s.block, s.lanes, s.pipelined, s.list_margin
+        return s.block, s.lanes, s.pipelined, s.list_margin, s.samples_per_thread
 
 
 def solve_noalloc(model: dict, params: dict, x_hat, ref, obstacles, u_nom, it: int, u_out=None, u_cmd=None,

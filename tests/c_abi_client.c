@@ -43,6 +43,7 @@ static void layout(void) {
     F(mppi_instance, reserved);
     S(mppi_shape);
     F(mppi_shape, block); F(mppi_shape, lanes); F(mppi_shape, pipelined); F(mppi_shape, list_margin);
+    F(mppi_shape, samples_per_thread);
     S(mppi_server_cfg);
     F(mppi_server_cfg, max_vehicles); F(mppi_server_cfg, slots); F(mppi_server_cfg, max_batch);
     F(mppi_server_cfg, N_max); F(mppi_server_cfg, M_max); F(mppi_server_cfg, queue_capacity);

@@ -62,11 +62,14 @@ def test_shape_validation(M):
     prob = I.plain_hover(K=512, N=10)
     s = M.Solver(prob["model"], prob["params"])
     for bad in ((128, 3, 0), (100, 1, 0), (128, 4, 1), (64, 2, 1), (1024, 1, 0), (128, 1, 0, -1.0),
-                (128, 1, 0, float("nan"))):
+                (128, 1, 0, float("nan")), (256, 1, 0, 0.0, 2), (128, 2, 0, 0.0, 2), (128, 1, 1, 0.0, 2),
+                (128, 1, 0, 0.0, 3)):
         with pytest.raises(M.MppiError):
             s.set_shape(*bad)
     s.set_shape(256, 32, 0, 0.5)
-    assert s.get_shape(512, 10, 0) == (256, 32, 0, 0.5)
+    assert s.get_shape(512, 10, 0) == (256, 32, 0, 0.5, 1)
+    s.set_shape(64, 1, 0, 0.5, 2)
+    assert s.get_shape(512, 10, 0) == (64, 1, 0, 0.5, 2)
     s.set_shape(0, 0, 0)
     assert s.get_shape(512, 10, 0)[:3] != (256, 32, 0)
     s.close()

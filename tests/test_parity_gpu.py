@@ -135,6 +135,7 @@ def test_every_launch_shape_matches_and_is_deterministic(M, orc, inp):
                (384, 2, 1, 0.0)]
     shapes += [(96, 1, 2, 0.0), (192, 1, 2, 0.0), (384, 1, 2, 0.0), (256, 2, 2, 0.0), (512, 2, 2, 0.0)]
     shapes += [(128, 1, 3, 0.0), (256, 1, 3, 0.0), (512, 1, 3, 0.0), (160, 2, 3, 0.0), (480, 2, 3, 0.0)]
+    shapes += [(64, 1, 0, 0.0, 2), (128, 1, 0, 0.0, 2), (128, 1, 0, 3.0, 2)]
     shapes += [(128, 1, 0, 0.25), (128, 4, 0, 3.0), (256, 1, 1, 2.0), (256, 32, 0, 0.5)]
     for shape in shapes:
         a = gpu_solve(M, prob, shape=shape)
@@ -177,6 +178,29 @@ def test_pipelined_form_matches_one_thread_per_sample(M, orc, inp, K, N, Mo):
     assert np.array_equal(four["costs"], two["costs"])
     for k in ("u_out", "u_next", "u_cmd"):
         assert control_err(four[k], two[k], sig) <= 1e-6, k
+
+
+@pytest.mark.parametrize("K,N,Mo", [(16384, 100, 64), (3001, 37, 40), (129, 5, 0), (1000, 1, 3)])
+def test_two_samples_per_thread_match_one(M, orc, inp, K, N, Mo):
+    """Two samples per thread run each sample's operations as one sample per
+    thread, packed across the two; the assembler fuses some packed
+    multiply-add pairs that the one-sample code rounds separately, so the
+    per-sample costs agree to FP32 rounding (measured: a few ulp), the update
+    too (the tiles also hold twice the samples, so the merge groups the
+    weighted sums differently), and both match the oracle; ragged tails
+    included."""
+    prob = inp.eight_with_spheres(K=K, N=N, M=max(Mo, 1), t0=0.9, **{"lambda": 150.0})
+    if Mo == 0:
+        prob["obstacles"] = np.zeros((0, 4), np.float32)
+    one = gpu_solve(M, prob, shape=(128, 1, 0))
+    sig = prob["params"]["sigma"]
+    for shape in ((64, 1, 0, 0.0, 2), (128, 1, 0, 0.0, 2)):
+        two = gpu_solve(M, prob, shape=shape)
+        assert cost_err(two["costs"], one["costs"])[0] <= 2e-6, shape
+        for k in ("u_out", "u_next", "u_cmd"):
+            assert control_err(two[k], one[k], sig) <= 1e-6, (shape, k)
+    if K * N <= 200000:
+        assert_step_close(prob, one, orc.mppi_step(prob, n_threads=16))
 
 
 def test_closed_loop_full_size(M, orc, inp):
