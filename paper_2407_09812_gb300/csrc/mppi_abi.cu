@@ -364,7 +364,7 @@ int launch_single(mppi_ctx* h, const mppi_instance& in, Shape s, cudaStream_t st
     a.N_max = in.N;
     a.M_max = in.M;
     const size_t smem = smem_bytes(in.N, in.M, s);
-    if (smem > 227 * 1024) return MPPI_EINVAL;
+    if (smem > kMaxDynamicSmem) return MPPI_EINVAL;
     cudaError_t e = launch_tiles(a, s, d.n_tiles, smem, st);
     return e == cudaSuccess ? MPPI_OK : MPPI_ECUDA;
 }
@@ -498,7 +498,7 @@ static int tune_on(mppi_ctx* h, mppi_instance in, cudaStream_t st, mppi_shape* b
     float bestT = 1e30f;
     int rc = MPPI_OK;
     auto time_shape = [&](const Shape& s) {
-        if (smem_bytes(in.N, in.M, s) > 227 * 1024) return;
+        if (smem_bytes(in.N, in.M, s) > kMaxDynamicSmem) return;
         // A candidate whose warm-up launch (and a second one: the first
         // may include loading the kernel) takes more than twice the best
         // so far is not timed further.
@@ -893,7 +893,7 @@ int mppi_solve_batch(mppi_handle h, const mppi_instance* instances, int32_t n, v
     if (rc) return rc;
     if ((rc = upload_batch(h, n, plan, st))) return rc;
     const size_t smem = smem_bytes(plan.N_b, plan.M_b, plan.s);
-    if (smem > 227 * 1024) return MPPI_EINVAL;
+    if (smem > kMaxDynamicSmem) return MPPI_EINVAL;
     if (cudaMemsetAsync(h->counters, 0, sizeof(unsigned), st) != cudaSuccess) return MPPI_ECUDA;
     LaunchArgs a = batch_args(h, plan);
     const int grid = std::min(plan.n_tiles, persistent_grid(plan.s, smem));
@@ -908,7 +908,7 @@ int mppi_solve_batch_graph(mppi_handle h, const mppi_instance* instances, int32_
     if (rc) return rc;
     if ((rc = upload_batch(h, n, plan, st))) return rc;
     const size_t smem = smem_bytes(plan.N_b, plan.M_b, plan.s);
-    if (smem > 227 * 1024) return MPPI_EINVAL;
+    if (smem > kMaxDynamicSmem) return MPPI_EINVAL;
     const std::pair<uint64_t, float> key(((uint64_t)plan.s.block << 48) | ((uint64_t)plan.s.lanes << 40) |
                                              ((uint64_t)plan.s.spt << 38) | ((uint64_t)plan.s.pipe << 36) |
                                              ((uint64_t)plan.N_b << 20) |

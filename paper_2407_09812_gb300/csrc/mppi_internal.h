@@ -145,6 +145,10 @@ bool aligned16(const void* p);
 bool aligned4(const void* p);
 
 size_t smem_bytes(int N_max, int M_max, Shape s);
+// Largest dynamic shared memory a launch may request: the 227 KB a block can
+// address less room for the kernel's static shared memory (under 8 KB in
+// every instantiation).
+constexpr size_t kMaxDynamicSmem = 227 * 1024 - 8 * 1024;
 bool shape_supported(Shape s);
 cudaError_t launch_tiles(const LaunchArgs& a, Shape s, int grid, size_t smem, cudaStream_t st);
 int max_active_blocks(Shape s, size_t smem);

@@ -89,7 +89,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model* model, const mppi_params* pa
 
     const Shape shape{kNoAllocBlock, 1};
     const size_t smem = smem_bytes(params->N, M, shape);
-    if (smem > 227 * 1024) return MPPI_EINVAL;
+    if (smem > kMaxDynamicSmem) return MPPI_EINVAL;
 
     float* scratch = nullptr;
     if ((rc = scratch_for_current_device(&scratch))) return rc;

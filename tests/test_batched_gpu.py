@@ -54,7 +54,8 @@ def _cap(probs):
             "N_max": max(p["params"]["N"] for p in probs), "M_max": 64}
 
 
-@pytest.mark.parametrize("graph,shape", [(False, (128, 2, 0)), (True, (128, 2, 0)), (True, (256, 1, 1))])
+@pytest.mark.parametrize("graph,shape", [(False, (128, 2, 0)), (True, (128, 2, 0)), (True, (256, 1, 1)),
+                                         (True, (128, 1, 0, 0.0, 2)), (False, (512, 1, 3))])
 def test_batch_matches_oracle_and_alone(M, orc, inp, graph, shape):
     import torch
     probs = _uneven(inp)

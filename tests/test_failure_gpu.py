@@ -22,7 +22,8 @@ def M():
     return mppi
 
 
-@pytest.mark.parametrize("shape", [(128, 1, 0), (128, 2, 0), (256, 1, 1), (384, 1, 2), (512, 1, 3)])
+@pytest.mark.parametrize("shape", [(128, 1, 0), (128, 2, 0), (256, 1, 1), (384, 1, 2), (512, 1, 3),
+                                   (128, 1, 0, 0.0, 2)])
 def test_timeout_reported_and_context_stays_usable(M, orc, inp, shape):
     prob = inp.eight_with_spheres(K=3000, N=24, M=32, t0=0.3, **{"lambda": 50.0})
     s = M.Solver(prob["model"], prob["params"])
