@@ -149,7 +149,8 @@ __device__ __forceinline__ uint2 philox_pre_tile(unsigned long long iter, const 
     return make_uint2(__umulhi(0xCD9E8D57u, lo) ^ rk[0].x, 0xCD9E8D57u * lo);
 }
 
-__device__ __forceinline__ float4 normals4_pre(unsigned j, const PhiloxPre p, const uint2* pt, const uint4* rk) {
+// The Philox output for step j from the precomputed first-round words.
+__device__ __forceinline__ uint4 philox_pre(unsigned j, const PhiloxPre p, const uint2* pt, const uint4* rk) {
     const uint2 t = *pt;
     uint4 c = make_uint4(t.x ^ j, t.y, p.z, p.w);
     c = philox_round(c, rk[0].z, rk[0].w);
@@ -159,7 +160,11 @@ __device__ __forceinline__ float4 normals4_pre(unsigned j, const PhiloxPre p, co
         c = philox_round(c, k.x, k.y);
         c = philox_round(c, k.z, k.w);
     }
-    return box_muller4(c);
+    return c;
+}
+
+__device__ __forceinline__ float4 normals4_pre(unsigned j, const PhiloxPre p, const uint2* pt, const uint4* rk) {
+    return box_muller4(philox_pre(j, p, pt, rk));
 }
 
 // delta = sigma o z, rounded once (no contraction) so that the rollout and
@@ -817,16 +822,6 @@ __device__ __forceinline__ U2 clamp_input_x2(const DevModel& M, U2 u) {
     return u;
 }
 
-// u_nom_j + sigma o z for the two samples' standard normals zA, zB.
-__device__ __forceinline__ U2 perturb_x2(const float4 un, const float4 zA, const float4 zB, const float* sigma) {
-    U2 u;
-    u.F = add2(bc(un.x), mul2(bc(sigma[0]), f2(zA.x, zB.x)));
-    u.wx = add2(bc(un.y), mul2(bc(sigma[1]), f2(zA.y, zB.y)));
-    u.wy = add2(bc(un.z), mul2(bc(sigma[2]), f2(zA.z, zB.z)));
-    u.wz = add2(bc(un.w), mul2(bc(sigma[3]), f2(zA.w, zB.w)));
-    return u;
-}
-
 __device__ __forceinline__ float2 input_cost_x2(const DevCost& C, const U2& u, const U2& up, bool rate) {
     const float2 tx = fma2(bc(C.R[2]), mul2(u.wy, u.wy), mul2(bc(C.R[0]), mul2(u.F, u.F)));
     const float2 ty = fma2(bc(C.R[3]), mul2(u.wz, u.wz), mul2(bc(C.R[1]), mul2(u.wx, u.wx)));
@@ -999,6 +994,54 @@ __device__ __forceinline__ float2 tracking_cost_x2(const DevCost& C, const State
     const float2 ev = add2(add2(mul2(dvx, dvx), mul2(dvy, dvy)), mul2(dvz, dvz));
     const float2 ew = fma2(dwz, dwz, add2(mul2(dwx, dwx), mul2(dwy, dwy)));
     return fma2(bc(C.c_p), ep, fma2(bc(C.c_q), mul2(d, d), fma2(bc(C.c_v), ev, mul2(bc(C.c_w), ew))));
+}
+
+// Box-Muller of box_muller4 for the two samples' Philox outputs rA, rB,
+// the float arithmetic packed across the samples.  Returns minus the
+// normals (rad cos, rad sin per pair): perturb_neg_x2 multiplies them by
+// -sigma, which rounds exactly as sigma times the normal.
+struct Z2 {
+    float2 z0, z1, z2, z3;
+};
+
+__device__ __forceinline__ float2 neg2log_x2(float2 u) {
+    float lx, ly;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lx) : "f"(u.x));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(ly) : "f"(u.y));
+    const float2 far = mul2(bc(-1.3862943611198906f), f2(lx, ly));
+    const float2 d = sub2(bc(1.0f), u);
+    const float2 near = mul2(d, fma2(d, fma2(d, fma2(d, bc(0.5f), bc(0.66666669f)), bc(1.0f)), bc(2.0f)));
+    return f2(d.x <= 0.015625f ? near.x : far.x, d.y <= 0.015625f ? near.y : far.y);
+}
+
+__device__ __forceinline__ Z2 box_muller_neg_x2(const uint4 rA, const uint4 rB) {
+    auto bits = [](unsigned ra, unsigned rb) {
+        return f2(__uint_as_float(0x3f800000u | (ra >> 9)), __uint_as_float(0x3f800000u | (rb >> 9)));
+    };
+    const float2 off = bc(0.99999994039535522f);
+    const float2 u0 = sub2(bits(rA.x, rB.x), off), u1 = sub2(bits(rA.y, rB.y), off);
+    const float2 u2 = sub2(bits(rA.z, rB.z), off), u3 = sub2(bits(rA.w, rB.w), off);
+    const float2 a01 = neg2log_x2(u0), a23 = neg2log_x2(u2);
+    const float2 r01 = mul2(a01, f2(rsqrtf(a01.x), rsqrtf(a01.y)));
+    const float2 r23 = mul2(a23, f2(rsqrtf(a23.x), rsqrtf(a23.y)));
+    const float2 t1 = fma2(bc(6.2831853071795865f), u1, bc(-3.1415926535897932f));
+    const float2 t3 = fma2(bc(6.2831853071795865f), u3, bc(-3.1415926535897932f));
+    float2 s1, c1, s3, c3;
+    __sincosf(t1.x, &s1.x, &c1.x);
+    __sincosf(t1.y, &s1.y, &c1.y);
+    __sincosf(t3.x, &s3.x, &c3.x);
+    __sincosf(t3.y, &s3.y, &c3.y);
+    return Z2{mul2(r01, c1), mul2(r01, s1), mul2(r23, c3), mul2(r23, s3)};
+}
+
+// u_nom_j + sigma o z with z = -zn (zn from box_muller_neg_x2).
+__device__ __forceinline__ U2 perturb_neg_x2(const float4 un, const Z2& zn, const float* sigma) {
+    U2 u;
+    u.F = add2(bc(un.x), mul2(bc(-sigma[0]), zn.z0));
+    u.wx = add2(bc(un.y), mul2(bc(-sigma[1]), zn.z1));
+    u.wy = add2(bc(un.z), mul2(bc(-sigma[2]), zn.z2));
+    u.wz = add2(bc(un.w), mul2(bc(-sigma[3]), zn.z3));
+    return u;
 }
 
 __device__ __forceinline__ void kahan_add_x2(float2& sum, float2& comp, float2 v) {
@@ -1419,9 +1462,9 @@ __global__ void __launch_bounds__(MINB > 1 ? 128 : 512, MINB) mppi_step_kernel(c
                 const uint4 pq = s_pp[tid];
                 PhiloxPre ppA, ppB;
                 ppA.z = pq.x; ppA.w = pq.y; ppB.z = pq.z; ppB.w = pq.w;
-                const float4 zA = normals4_pre((unsigned)j, ppA, &s_pt, s_rk);
-                const float4 zB = normals4_pre((unsigned)j, ppB, &s_pt, s_rk);
-                const U2 u = clamp_input_x2(Mdl, perturb_x2(su[j], zA, zB, sigma));
+                const Z2 zn = box_muller_neg_x2(philox_pre((unsigned)j, ppA, &s_pt, s_rk),
+                                                philox_pre((unsigned)j, ppB, &s_pt, s_rk));
+                const U2 u = clamp_input_x2(Mdl, perturb_neg_x2(su[j], zn, sigma));
                 U2 u_prev;
                 {
                     const float4 a = s_up[2 * tid], b = s_up[2 * tid + 1];
