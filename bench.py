@@ -59,6 +59,12 @@ CLOSED_LOOP = ("closed-loop figure-eight tracking, K=16384, N=100, dt=0.01 s, 64
 # the kernel reports how many pairs it evaluated (mppi_set_counters).
 FLOP_PER_STEP = 650
 FLOP_PER_PAIR = 17
+# The counting launch runs one thread per sample (each warp culls with the
+# box of its 32 samples' positions, the finest culling of any shape), so the
+# work counted does not depend on the shape that is timed: two samples per
+# thread cull with a box over 64 positions and evaluate a few more pairs
+# that add exactly zero.
+COUNT_SHAPE = (128, 1, 0)
 MUFU_PER_STEP = {"lg2_ops": 2, "rsqrt_ops": 3, "sin_ops": 2, "cos_ops": 2}
 MUFU_PER_PAIR = {"ex2_ops": 1}
 
@@ -348,11 +354,16 @@ def run_fleet(args, rank: int, peaks: dict, clk: ClockSampler):
         shape = solver.autotune_batch(fleet.dicts(bufs), stream=stream)
     t_tune = time.perf_counter() - t_tune
     pairs = torch.zeros(1, dtype=torch.int64, device="cuda")
+    solver.set_shape(*COUNT_SHAPE)
     solver.set_counters(pairs)  # evaluated obstacle pairs of step 0, in an untimed launch
     solver.solve_batch(rec[0], stream=stream, graph=False)
     torch.cuda.synchronize()
     pairs_per_launch = int(pairs.item())
     solver.set_counters(None)
+    if args.shape:
+        solver.set_shape(*shape)
+    else:
+        solver.set_shape(0, 0, 0)  # back to the tuned shape
     flush = flusher()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_total)]
 
@@ -608,11 +619,13 @@ def run_stress(peaks: dict, reps=3, shape=None):
                                "dt": prob["params"]["dt"], "lambda": prob["params"]["lambda"],
                                "sigma": prob["params"]["sigma"], "seed": prob["params"]["seed"], "iter": 0})
     pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+    s.set_shape(*COUNT_SHAPE)
     s.set_counters(pairs)
     s.solve_async(x, r, o, u, prob["iter"], u_out=out["u_out"])
     torch.cuda.synchronize()
     n_pairs = int(pairs.item())
     s.set_counters(None)
+    s.set_shape(*shape)
     flush = flusher()
     ts = []
     for i in range(reps):

@@ -108,13 +108,14 @@ def test_temperature_limits_and_zero_noise(M, orc, inp):
             assert np.array_equal(g["u_out"], prob["u_nom"])
 
 
+@pytest.mark.parametrize("shape", [None, (128, 1, 0, 0.0, 2), (512, 1, 3)])
 @pytest.mark.parametrize("over", [{"quat_metric": 1}, {"tail_mode": 1}, {"shift_alpha": 0.25},
                                   {"delay": 0.004}, {"lambda": 20.0, "shift_alpha": 0.1, "tail_mode": 1}])
-def test_step_options(M, orc, inp, over):
+def test_step_options(M, orc, inp, over, shape):
     base = inp.eight_with_spheres(K=1500, N=25, M=20, t0=0.7)
     prob = dict(base, params=dict(base["params"], **over))
     ref = orc.mppi_step(prob, n_threads=8)
-    assert_step_close(prob, gpu_solve(M, prob), ref)
+    assert_step_close(prob, gpu_solve(M, prob, shape=shape), ref)
 
 
 def test_nonfinite_state_reports_and_keeps_nominal(M, inp):
@@ -252,9 +253,11 @@ def test_maximum_sizes(M, orc, inp):
     print("K_MAX errors", e, "ess", 1.0 / np.sum(ref["weights"] ** 2))
 
 
-def test_grid_collision_module(M, orc, inp):
+@pytest.mark.parametrize("shape", [None, (128, 1, 0, 0.0, 2), (512, 1, 3)])
+def test_grid_collision_module(M, orc, inp, shape):
     """Occupancy voxel grid as the collision module (with spheres too):
-    the GPU's per-state lookup and indicator match the oracle."""
+    the GPU's per-state lookup and indicator match the oracle (one thread
+    per sample, two samples per thread, the split pipelined form)."""
     import torch
     prob = inp.eight_with_spheres(K=2048, N=40, M=16, t0=0.9, **{"lambda": 300.0})
     rng = np.random.default_rng(21)
@@ -267,6 +270,8 @@ def test_grid_collision_module(M, orc, inp):
     ref = orc.mppi_step(prob, n_threads=8)
     assert np.mean(ref["costs"] >= prob["params"]["c_obs"]) > 0.05  # the grid is hit by many rollouts
     s = M.Solver(prob["model"], prob["params"])
+    if shape:
+        s.set_shape(*shape)
     s.set_grid(torch.from_numpy(occ).cuda(), origin, voxel)
     g = s.solve(prob["x_hat"], prob["ref"], prob["obstacles"], prob["u_nom"], prob["iter"], want_costs=True)
     e = assert_step_close(prob, g, ref)
@@ -277,15 +282,19 @@ def test_grid_collision_module(M, orc, inp):
     print("grid module errors", e)
 
 
-def test_evaluated_pair_counter(M, orc, inp):
+@pytest.mark.parametrize("shape", [None, (128, 1, 0, 0.0, 2)])
+def test_evaluated_pair_counter(M, orc, inp, shape):
     """The measurement hook counts evaluated (state, obstacle) pairs: all of
     them when nothing can be culled (beta = 0: the barrier never vanishes),
-    fewer with the default barrier; the results stay within tolerance."""
+    fewer with the default barrier; the results stay within tolerance (ragged
+    last tile included)."""
     import torch
     prob = inp.eight_with_spheres(K=1000, N=20, M=40, t0=0.2)
     for beta, exact in ((0.0, True), (1.0, False)):
         p = dict(prob, params=dict(prob["params"], beta=beta))
         s = M.Solver(p["model"], p["params"])
+        if shape:
+            s.set_shape(*shape)
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
         s.set_counters(cnt)
         g = s.solve(p["x_hat"], p["ref"], p["obstacles"], p["u_nom"], p["iter"], want_costs=True)
@@ -300,7 +309,7 @@ def test_evaluated_pair_counter(M, orc, inp):
 
 
 @pytest.mark.parametrize("shape", [(128, 1, 0), (256, 1, 1), (128, 2, 0), (384, 2, 1), (128, 1, 0, 0.25),
-                                   (256, 1, 1, 3.0), (256, 32, 0)])
+                                   (256, 1, 1, 3.0), (256, 32, 0), (128, 1, 0, 0.5, 2), (512, 1, 3, 1.0)])
 def test_reused_kept_lists_equal_per_step_culling(M, inp, shape):
     """A warp's kept-obstacle list is built for its box grown by a margin and
     reused while its positions stay inside; launches that count evaluated
