@@ -73,9 +73,9 @@ MUFU_PER_PAIR = {"ex2_ops": 1}
 # kernel source it was taken with (sha256 of the kernel file and its header,
 # first 16 hex digits); any other source reports null.
 TRAFFIC_CAPTURES = {
-    "fleet": {"kernel_sha": "42053d89251e07ce", "bytes": 2147584},
-    "closed_loop": {"kernel_sha": "42053d89251e07ce", "bytes": 118784},
-    "stress": {"kernel_sha": "42053d89251e07ce", "bytes": 134144},
+    "fleet": {"kernel_sha": "245671fd48323a82", "bytes": 2146048},
+    "closed_loop": {"kernel_sha": "245671fd48323a82", "bytes": 118272},
+    "stress": {"kernel_sha": "245671fd48323a82", "bytes": 120064},
 }
 KERNEL_FILES = ("paper_2407_09812_gb300/csrc/mppi_kernels.cu", "paper_2407_09812_gb300/csrc/mppi_internal.h")
 
