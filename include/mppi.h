@@ -301,7 +301,9 @@ int mppi_set_wait_limit(mppi_handle h, int64_t polls, int32_t stall_obstacle_cop
 
 /* Launch shape of the rollout kernel. */
 typedef struct {
-    int32_t block;          /* threads per block: 64, 128, 256 or 512       */
+    int32_t block;          /* threads per block: 64, 128, 256 or 512; for
+                               the pipelined forms a multiple of
+                               32 (pipelined + lanes) up to 512             */
     int32_t lanes;          /* lanes per sample: 1 (one thread per sample),
                                2, 4, 8 or 32 (warp split of the obstacle
                                loop; 32: one sample per warp)               */
@@ -342,7 +344,8 @@ typedef struct {
 int mppi_set_shape(mppi_handle h, const mppi_shape* shape);
 
 /* Project autotuner (the paper has no counterpart): times every candidate shape (block size, samples per
- * warp, pipelined form, then the obstacle tiling of the fastest) on a
+ * warp or two samples per thread, pipelined forms 1-3, then the obstacle
+ * tiling of the fastest) on a
  * synthetic problem of size (K, N, M) on `stream`, stores the fastest in
  * the handle's table for that size bucket and returns it in *best (may be
  * NULL).  Synchronous. */
