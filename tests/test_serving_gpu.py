@@ -186,3 +186,33 @@ def test_remove_vehicle_with_pending_requests(S, orc, inp):
     got2 = _collect(srv, 1)
     assert np.array_equal(got2[r2]["u0"], got[rids[1]]["u0"])  # fresh vehicle: same nominal and counter
     srv.close()
+
+
+def test_default_shapes_large_batches_match_oracle(S, orc, inp):
+    """No forced shape: the server's batched launches take the default shape
+    for their size, here two samples per thread (each batch holds well over
+    one 256-sample tile per SM); every result matches the FP64 oracle."""
+    rng = np.random.default_rng(11)
+    probs = []
+    for i in range(12):
+        N = 25
+        ref = inp.Trajectory("eight", {"phase": float(rng.uniform(0, 6))}).window(0.0, N, 0.01)
+        x = ref[0].copy()
+        x[0:3] += rng.uniform(-0.5, 0.5, 3).astype(np.float32)
+        obs = inp.spheres(rng, 8, (-20, -10, 0), (20, 10, 5), 0.3, 1.0)
+        p = inp.params(K=8192, N=N, dt=0.01, seed=500 + i, stream_id=i, **{"lambda": 50.0})
+        probs.append(inp.problem(inp.model(motor_clip=1), p, x, ref, obs, inp.hover_u(inp.model(), N), it=0))
+    srv = S.Server(inp.model(motor_clip=1), inp.params(),
+                   {"max_vehicles": 12, "slots": 2, "max_batch": 8, "N_max": 25, "M_max": 8,
+                    "queue_capacity": 64, "max_batch_samples": 8 * 8192, "hbm_budget_bytes": 2 << 30,
+                    "block": 0, "lanes": 0})
+    vids = [_add(srv, p) for p in probs]
+    rids = [srv.submit(v, p["x_hat"], p["ref"]) for v, p in zip(vids, probs)]
+    res = _collect(srv, len(rids))
+    srv.close()
+    assert max(r["batch_size"] for r in res.values()) > 4
+    for rid, p in zip(rids, probs):
+        r = res[rid]
+        assert r["status"] == 0
+        ref = orc.mppi_step(p, n_threads=8)
+        assert control_err(r["u0"], ref["u_out"][0], p["params"]["sigma"]) <= U_RTOL
