@@ -127,26 +127,37 @@ uint64_t bucket_key(long long K, int N, int M) {
     return ((uint64_t)ceil_log2(K) << 16) | ((uint64_t)ceil_log2(N) << 8) | (uint64_t)(M > 0 ? ceil_log2(M) + 1 : 0);
 }
 
-Shape default_shape(long long K, int N, int M) {
-    (void)N;
-    // Fewer 128-sample tiles than SMs and a real obstacle set: the step is
-    // bound by each warp's dependent chain, and the pipelined form (a
-    // dynamics and a cost thread per sample, separate warps) overlaps the
-    // obstacle scoring with the integration.  Enough samples for a
-    // 256-sample tile on every SM: the launch is bound by issue rate, and two
-    // samples per thread (packed arithmetic) issue fewer instructions;
-    // otherwise one thread per sample.  The autotuner refines per size
-    // bucket.
-    const long long sms = (long long)mppi::sm_count();
-    if ((K + 127) / 128 < sms && M >= 16) return Shape{256, 1, 1};
-    if ((K + 255) / 256 >= sms) return Shape{128, 1, 0, 0.0f, 2};
-    return Shape{128, 1, 0};
-}
-
 int bucket_pow2(int v, int lo) {
     int b = lo;
     while (b < v) b <<= 1;
     return b;
+}
+
+Shape default_shape(long long K, int N, int M) {
+    // At most one tile per SM: the step is bound by each warp's chain of
+    // dependent operations, and the split pipelined form (noise, attitude,
+    // translation and cost threads of a sample in separate warps) shortens
+    // the chain; the smallest tile (32, 64 or 128 samples) that still gives
+    // at most one tile per SM spreads the samples over the most SMs.
+    // Measured (median of 40 solves after an L2 flush): K=1024, N=50, no
+    // obstacles 37.5 -> 29.3 us against one thread per sample; K=2048, N=50,
+    // 32 spheres 45.7 -> 35.5 us and K=8192, N=100, 32 spheres 74.4 -> 60.0
+    // us against the two-warp pipelined form.  Enough samples for a
+    // 256-sample tile on every SM: the launch is bound by issue rate, and two
+    // samples per thread (packed arithmetic) issue fewer instructions;
+    // otherwise one thread per sample.  The autotuner refines per size
+    // bucket.  The shared-memory check uses the batched launch's bucketed
+    // capacity (a power of two at least N, resp. M).
+    const long long sms = (long long)mppi::sm_count();
+    for (int spb : {32, 64, 128}) {
+        if ((K + spb - 1) / spb > sms) continue;
+        const Shape s{4 * spb, 1, 3};
+        if (mppi::smem_bytes(bucket_pow2(N, 16), M > 0 ? bucket_pow2(M, 16) : 0, s) <= mppi::kMaxDynamicSmem)
+            return s;
+        break;
+    }
+    if ((K + 255) / 256 >= sms) return Shape{128, 1, 0, 0.0f, 2};
+    return Shape{128, 1, 0};
 }
 
 }  // namespace

@@ -75,6 +75,32 @@ def test_shape_validation(M):
     s.close()
 
 
+def test_default_shapes(M):
+    """Untuned sizes take the default for their tile count on this GPU: at
+    most one tile per SM, the split pipelined form with the smallest tile
+    (32, 64, 128 samples) that keeps it so, unless its shared memory does
+    not fit; at least one 256-sample tile per SM, two samples per thread;
+    one thread per sample in between."""
+    import torch
+    from paper_2407_09812_gb300 import inputs as I
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    prob = I.plain_hover(K=512, N=10)
+    s = M.Solver(prob["model"], prob["params"])
+    assert s.get_shape(1024, 50, 0)[:3] == (128, 1, 3)
+    assert s.get_shape(32 * sms, 100, 64)[:3] == (128, 1, 3)
+    assert s.get_shape(32 * sms + 1, 100, 64)[:3] == (256, 1, 3)
+    assert s.get_shape(128 * sms, 100, 64)[:3] == (512, 1, 3)
+    assert s.get_shape(128 * sms + 1, 100, 64)[:3] == (128, 1, 0)
+    for K in (256 * sms - 255, 1 << 20):
+        got = s.get_shape(K, 200, 1024)
+        assert got[:3] == (128, 1, 0) and got[4] == 2, (K, got)
+    assert s.get_shape(256 * sms - 256, 100, 64)[4] == 1
+    # The largest horizon with the largest obstacle set: the split form's
+    # rings do not fit beside them, one thread per sample is taken.
+    assert s.get_shape(1024, M.N_MAX, M.M_MAX)[2] == 0
+    s.close()
+
+
 def test_plain_c_client_solves_like_the_binding(M, inp, tmp_path):
     """A C99 program that includes only include/mppi.h and links the library
     gets, through mppi_solve, bitwise the results of the Python binding."""
