@@ -371,13 +371,17 @@ int mppi_autotune_batch(mppi_handle h, const mppi_instance* instances, int32_t n
 /* Looks up the shape the handle uses for a problem of size (K, N, M)
  * (the paper has no counterpart): the forced shape, else the tuned one
  * for the size bucket, else the default for a launch of K samples on this
- * GPU's S multiprocessors: at most one tile per multiprocessor
- * (K <= 128 S), pipelined form 3 with the smallest tile of 32, 64 or 128
- * samples (block 128, 256 or 512) that keeps it so, when its shared memory
- * fits; K > 256 (S - 1), two samples per thread in blocks of 128;
- * otherwise one thread per sample in blocks of 128.  For a batch the
- * default takes its total K (the tuning table its mean K), largest N and
- * largest M. */
+ * GPU's S multiprocessors:
+ *   K <= 128 S: pipelined form 3 with the smallest tile of 32, 64 or 128
+ *     samples (block 128, 256 or 512) that keeps one tile per
+ *     multiprocessor, when its shared memory fits;
+ *   K <= 256 S and M >= 16: pipelined form 1, block 256 (128 samples);
+ *   K > 256 (S - 1): two samples per thread in blocks of 128, unless the
+ *     busiest multiprocessor gets more than 8 % more samples with
+ *     256-sample tiles than with 128-sample tiles;
+ *   otherwise one thread per sample in blocks of 128.
+ * For a batch the default takes its total K (the tuning table its mean K),
+ * largest N and largest M. */
 int mppi_get_shape(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* shape);
 
 /* ---------------------------------------------------------------------

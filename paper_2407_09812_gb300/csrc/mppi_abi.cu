@@ -134,29 +134,46 @@ int bucket_pow2(int v, int lo) {
 }
 
 Shape default_shape(long long K, int N, int M) {
-    // At most one tile per SM: the step is bound by each warp's chain of
-    // dependent operations, and the split pipelined form (noise, attitude,
-    // translation and cost threads of a sample in separate warps) shortens
-    // the chain; the smallest tile (32, 64 or 128 samples) that still gives
-    // at most one tile per SM spreads the samples over the most SMs.
-    // Measured (median of 40 solves after an L2 flush): K=1024, N=50, no
-    // obstacles 37.5 -> 29.3 us against one thread per sample; K=2048, N=50,
-    // 32 spheres 45.7 -> 35.5 us and K=8192, N=100, 32 spheres 74.4 -> 60.0
-    // us against the two-warp pipelined form.  Enough samples for a
-    // 256-sample tile on every SM: the launch is bound by issue rate, and two
-    // samples per thread (packed arithmetic) issue fewer instructions;
-    // otherwise one thread per sample.  The autotuner refines per size
-    // bucket.  The shared-memory check uses the batched launch's bucketed
+    // Chosen by tile count on this GPU's S SMs (median of 15-40 solves after
+    // an L2 flush, figure-eight problems; the autotuner refines per size
+    // bucket).  The shared-memory checks use the batched launch's bucketed
     // capacity (a power of two at least N, resp. M).
-    const long long sms = (long long)mppi::sm_count();
+    //  1. At most one tile per SM: the step is bound by each warp's chain of
+    //     dependent operations, and the split pipelined form (noise,
+    //     attitude, translation and cost threads of a sample in separate
+    //     warps) shortens the chain; the smallest tile (32, 64 or 128
+    //     samples) that keeps one tile per SM spreads the samples over the
+    //     most SMs.  K=1024, N=50, no obstacles 37.5 -> 29.3 us against one
+    //     thread per sample; K=2048, N=50, 32 spheres 45.7 -> 35.5 us and
+    //     K=8192, N=100 74.4 -> 60.0 us against the two-warp form.
+    //  2. At most two 128-sample tiles per SM and an obstacle set: the
+    //     two-warp pipelined form (dynamics and cost threads), which overlaps
+    //     the scoring with the integration.  K=32768, N=100, 32 spheres 115.3
+    //     -> 105.1 us against one thread per sample.
+    //  3. At least one 256-sample tile per SM: two samples per thread
+    //     (packed arithmetic, fewer instructions), unless the last wave of
+    //     256-sample tiles leaves the SMs much less evenly loaded than that
+    //     of 128-sample tiles (largest per-SM share of the samples more than
+    //     8 % above, the packed form's gain): K=49152, N=100, 32 spheres 172.7
+    //     -> 148.1 us with one thread per sample.  Otherwise one thread per
+    //     sample.
+    const long long S = (long long)mppi::sm_count();
+    const int Nb = bucket_pow2(N, 16), Mb = M > 0 ? bucket_pow2(M, 16) : 0;
     for (int spb : {32, 64, 128}) {
-        if ((K + spb - 1) / spb > sms) continue;
+        if ((K + spb - 1) / spb > S) continue;
         const Shape s{4 * spb, 1, 3};
-        if (mppi::smem_bytes(bucket_pow2(N, 16), M > 0 ? bucket_pow2(M, 16) : 0, s) <= mppi::kMaxDynamicSmem)
-            return s;
+        if (mppi::smem_bytes(Nb, Mb, s) <= mppi::kMaxDynamicSmem) return s;
         break;
     }
-    if ((K + 255) / 256 >= sms) return Shape{128, 1, 0, 0.0f, 2};
+    const long long t128 = (K + 127) / 128, t256 = (K + 255) / 256;
+    if (M >= 16 && t128 <= 2 * S) {
+        const Shape s{256, 1, 1};
+        if (mppi::smem_bytes(Nb, Mb, s) <= mppi::kMaxDynamicSmem) return s;
+    }
+    if (t256 >= S) {
+        const long long load2 = (t256 + S - 1) / S * 256, load1 = (t128 + S - 1) / S * 128;
+        if (load2 * 25 <= load1 * 27) return Shape{128, 1, 0, 0.0f, 2};
+    }
     return Shape{128, 1, 0};
 }
 

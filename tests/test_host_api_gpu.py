@@ -76,28 +76,37 @@ def test_shape_validation(M):
 
 
 def test_default_shapes(M):
-    """Untuned sizes take the default for their tile count on this GPU: at
-    most one tile per SM, the split pipelined form with the smallest tile
-    (32, 64, 128 samples) that keeps it so, unless its shared memory does
-    not fit; at least one 256-sample tile per SM, two samples per thread;
-    one thread per sample in between."""
+    """Untuned sizes take the default for their tile count on this GPU's S
+    SMs: at most one tile per SM, the split pipelined form with the smallest
+    tile (32, 64, 128 samples) that keeps it so, unless its shared memory
+    does not fit; at most two 128-sample tiles per SM with 16 or more
+    obstacles, the two-warp pipelined form; from one 256-sample tile per SM
+    on, two samples per thread unless the last wave of 256-sample tiles
+    loads the SMs more than 8 % less evenly than 128-sample tiles; else one
+    thread per sample."""
     import torch
     from paper_2407_09812_gb300 import inputs as I
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    S = torch.cuda.get_device_properties(0).multi_processor_count
     prob = I.plain_hover(K=512, N=10)
     s = M.Solver(prob["model"], prob["params"])
-    assert s.get_shape(1024, 50, 0)[:3] == (128, 1, 3)
-    assert s.get_shape(32 * sms, 100, 64)[:3] == (128, 1, 3)
-    assert s.get_shape(32 * sms + 1, 100, 64)[:3] == (256, 1, 3)
-    assert s.get_shape(128 * sms, 100, 64)[:3] == (512, 1, 3)
-    assert s.get_shape(128 * sms + 1, 100, 64)[:3] == (128, 1, 0)
-    for K in (256 * sms - 255, 1 << 20):
-        got = s.get_shape(K, 200, 1024)
-        assert got[:3] == (128, 1, 0) and got[4] == 2, (K, got)
-    assert s.get_shape(256 * sms - 256, 100, 64)[4] == 1
-    # The largest horizon with the largest obstacle set: the split form's
-    # rings do not fit beside them, one thread per sample is taken.
-    assert s.get_shape(1024, M.N_MAX, M.M_MAX)[2] == 0
+    shape = lambda K, N, Mo: s.get_shape(K, N, Mo)[:3] + s.get_shape(K, N, Mo)[4:]
+    assert shape(1024, 50, 0) == (128, 1, 3, 1)
+    assert shape(32 * S, 100, 64) == (128, 1, 3, 1)
+    assert shape(32 * S + 1, 100, 64) == (256, 1, 3, 1)
+    assert shape(128 * S, 100, 0) == (512, 1, 3, 1)
+    for K in (128 * S + 1, 256 * S):
+        assert shape(K, 100, 64) == (256, 1, 1, 1), K
+    assert shape(128 * S + 1, 100, 8) == (128, 1, 0, 1)
+    assert shape(256 * S, 100, 8) == (128, 1, 0, 2)
+    # 256 S + 1 samples: three 128-sample tiles on the busiest SM against two
+    # 256-sample tiles (512 samples), one thread per sample; an exact
+    # multiple of 256 S: two samples per thread.
+    assert shape(256 * S + 1, 100, 64) == (128, 1, 0, 1)
+    assert shape(7 * 256 * S, 200, 1024) == (128, 1, 0, 2)
+    assert shape(1 << 22, 100, 32) == (128, 1, 0, 2)
+    # The largest horizon with the largest obstacle set: the pipelined
+    # forms' rings do not fit beside them, one thread per sample is taken.
+    assert shape(1024, M.N_MAX, M.M_MAX) == (128, 1, 0, 1)
     s.close()
 
 
