@@ -1083,6 +1083,12 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
     // M obstacles (spheres and, every third, vertical cylinders, radii
     // 0.3-1.0 m) at fixed pseudo-random places, starting 0.5 m off the line:
     // the rollouts spread and only nearby obstacles matter, as in flight.
+    // Above 64 obstacles the box grows in x and y with sqrt(M / 64), so that
+    // the obstacle density along the line (and the kept-obstacle lists) stay
+    // those of 64 obstacles in 40 x 20 x 5 m, the density of the workloads
+    // the library is measured on; a fixed box would pack 1024 obstacles 16
+    // times denser than any of them and favour the forms built for heavy
+    // obstacle scoring.
     std::vector<float> xh(13, 0.0f), ref(13 * (size_t)(N + 1), 0.0f), u(4 * (size_t)N, 0.0f), obs(4 * (size_t)M);
     const float dt = h->params.dt, speed = 8.0f;
     xh[0] = -10.0f; xh[1] = 0.5f; xh[2] = 2.5f; xh[3] = 1.0f; xh[7] = speed;
@@ -1096,9 +1102,10 @@ int mppi_autotune(mppi_handle h, int32_t K, int32_t N, int32_t M, mppi_shape* be
         lcg = lcg * 1664525u + 1013904223u;
         return (float)(lcg >> 8) * (1.0f / 16777216.0f);
     };
+    const float grow = M > 64 ? std::sqrt((float)M / 64.0f) : 1.0f;
     for (int o = 0; o < M; ++o) {
-        obs[4 * o + 0] = -20.0f + 40.0f * unif();
-        obs[4 * o + 1] = -10.0f + 20.0f * unif();
+        obs[4 * o + 0] = grow * (-20.0f + 40.0f * unif());
+        obs[4 * o + 1] = grow * (-10.0f + 20.0f * unif());
         obs[4 * o + 2] = 5.0f * unif();
         const float rad = 0.3f + 0.7f * unif();
         obs[4 * o + 3] = (o % 3 == 2) ? -rad : rad;
