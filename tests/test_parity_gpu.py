@@ -67,6 +67,26 @@ def test_plain_hover_full_size(M, orc, inp):
     print("plain hover errors", e)
 
 
+@pytest.mark.parametrize("tiles", ["32S", "32S+1", "128S+1", "256S+1", "512S"])
+def test_default_shape_regimes_match_oracle(M, orc, inp, tiles):
+    """Untuned sizes in each regime of the default launch shape on this GPU's
+    S SMs (split pipelined form with 32- and 64-sample tiles, two-warp
+    pipelined form, one thread per sample, two samples per thread), ragged
+    where the regime allows, through the host-buffer entry point, against
+    the full FP64 oracle step."""
+    import torch
+    S = torch.cuda.get_device_properties(0).multi_processor_count
+    K = {"32S": 32 * S, "32S+1": 32 * S + 1, "128S+1": 128 * S + 1, "256S+1": 256 * S + 1, "512S": 512 * S}[tiles]
+    prob = inp.eight_with_spheres(K=K, N=9, M=24, t0=0.6, **{"lambda": 150.0})
+    want = {"32S": (128, 1, 3, 1), "32S+1": (256, 1, 3, 1), "128S+1": (256, 1, 1, 1), "256S+1": (128, 1, 0, 1),
+            "512S": (128, 1, 0, 2)}[tiles]
+    s = M.Solver(prob["model"], prob["params"])
+    got = s.get_shape(K, 9, 24)
+    s.close()
+    assert got[:3] + got[4:] == want, got
+    assert_step_close(prob, gpu_solve(M, prob), orc.mppi_step(prob, n_threads=os.cpu_count() or 1))
+
+
 @pytest.mark.parametrize("K,N", [(1, 1), (7, 3), (129, 5), (1000, 17), (4097, 2), (300, 130)])
 def test_ragged_sizes(M, orc, inp, K, N):
     prob = inp.plain_hover(K=K, N=N, dt=0.02, seed=K * 31 + N)
