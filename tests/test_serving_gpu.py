@@ -190,8 +190,9 @@ def test_remove_vehicle_with_pending_requests(S, orc, inp):
 
 def test_default_shapes_large_batches_match_oracle(S, orc, inp):
     """No forced shape: the server's batched launches take the default shape
-    for their size, here two samples per thread (each batch holds well over
-    one 256-sample tile per SM); every result matches the FP64 oracle."""
+    for their total size (up to 8 vehicles of 8192 samples: from two samples
+    per thread down to the split pipelined form, by the batch's tile count);
+    every result matches the FP64 oracle."""
     rng = np.random.default_rng(11)
     probs = []
     for i in range(12):
