@@ -98,9 +98,13 @@ def captured_traffic(workload: str):
 # ---------------------------------------------------------------- helpers
 
 class ClockSampler:
-    """nvidia-smi SM clocks and throttle reasons, sampled every 100 ms from
-    before the first GPU section to the end of the last one; each sample
-    carries the host time it arrived, so a section's share can be picked."""
+    """nvidia-smi SM clocks and throttle reasons, sampled every LOOP_MS ms
+    from before the first GPU section to the end of the last one; each
+    sample carries the host time it arrived, so a section's share can be
+    picked (20 ms: a few samples fall inside even a 20-step timed region of
+    the headline, 90 ms long)."""
+
+    LOOP_MS = 20
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -116,7 +120,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.LOOP_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
             t0 = time.time()
@@ -1022,7 +1026,8 @@ def main():
             line["serving"] = {"unavailable": str(e)[:200]}
     clk.stop()
     line["clocks"] = clk.summary()
-    line["clocks"]["window"] = "every 100 ms from before the first GPU section to the end of the last"
+    line["clocks"]["window"] = (f"every {ClockSampler.LOOP_MS} ms from before the first GPU section to the end "
+                                f"of the last")
     line["clocks"]["headline_samples"] = clk.summary(*res["window"])["samples"]
     line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if stress_in and not args.no_oracle:
