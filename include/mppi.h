@@ -218,7 +218,8 @@ typedef struct {
  * mppi_solve_async; batching is this library's, not the paper's).  `instances` is a
  * HOST array of n descriptors (copied before return).  The launch shape
  * (block size, samples per warp) is taken from the handle's tuning table
- * (mppi_autotune) or a default.  Every instance's result equals what
+ * (mppi_autotune) or the default for the batch's total K, largest N and
+ * largest M (mppi_get_shape).  Every instance's result equals what
  * mppi_solve_async returns for it alone with the same launch shape. */
 int mppi_solve_batch(mppi_handle h, const mppi_instance* instances, int32_t n, void* stream);
 
