@@ -841,13 +841,13 @@ def run_serving(args):
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_on_fleet(probs, budget_s: float):
+def oracle_on_fleet(probs, budget_s: float, threads: int = 0):
     """Solves fleet instances with the FP64 oracle (OpenMP over each
-    instance's samples, all host cores), in order, until `budget_s` has
-    passed (at least one, at most all); returns (rollout-steps, solves,
-    seconds)."""
+    instance's samples, all host cores unless `threads` is given), in order,
+    until `budget_s` has passed (at least one, at most all); returns
+    (rollout-steps, solves, seconds)."""
     from oracle import oracle as O
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     steps = n = 0
     t0 = time.perf_counter()
     while True:
@@ -860,6 +860,21 @@ def oracle_on_fleet(probs, budget_s: float):
             return steps, n, el
 
 
+def host_cpu() -> str:
+    """Architecture and CPU model of the host (lscpu, best effort)."""
+    import platform
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return f"{platform.machine()}, {model}" if model else platform.machine()
+
+
 def cpu_baseline(seconds: float):
     """The FP64 oracle as it stands, OpenMP over all host cores, on the
     fleet's instances in order until about `seconds` have passed; rates are
@@ -867,9 +882,16 @@ def cpu_baseline(seconds: float):
     from paper_2407_09812_gb300 import inputs as I
     probs = I.batched_uneven(n=N_FLEET, seed=FLEET_SEED, dt=FLEET_DT)
     steps, n, el = oracle_on_fleet(probs, seconds)
-    return {"value": steps / el, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+    # The same on one host thread, on the smallest instances (a shorter
+    # sample): the oracle's own per-core rate, for the OpenMP leg's scaling.
+    small = sorted(probs, key=lambda p: p["params"]["K"] * p["params"]["N"])
+    s1, n1, el1 = oracle_on_fleet(small, max(1.0, seconds / 4), threads=1)
+    return {"value": steps / el, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle", "cpu": host_cpu(),
             "sample": f"the first {n} of the 256 fleet instances in order, each one full FP64 solve, in {el:.1f} s",
-            "solves_per_s": n / el}
+            "solves_per_s": n / el,
+            "single_thread": {"value": s1 / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"the {n1} smallest fleet instances (K N), one full FP64 solve each on one "
+                                        f"host thread, in {el1:.1f} s"}}
 
 
 def reference_arm(args) -> dict:
@@ -914,8 +936,8 @@ def reference_arm(args) -> dict:
             "impl": "reference", "solves_per_s": per_step * len(times) / float(times.sum()),
             "latency_ms": {"p50": float(np.percentile(times, 50) * 1e3),
                            "p99": float(np.percentile(times, 99) * 1e3)},
-            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count() or 1, "sample": sample, "value": value,
-                             "unit": UNIT},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count() or 1, "cpu": host_cpu(), "sample": sample,
+                             "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_all}
 
