@@ -269,3 +269,34 @@ def test_batch_autotuner_times_the_batch_and_leaves_it_untouched(M, orc, inp):
         assert_step_close(p, _host(d), orc.mppi_step(p, n_threads=8))
     s.close()
     print("autotune_batch", best)
+
+
+def test_headline_fleet_full_size_sampled(M, orc, inp):
+    """The benchmark's headline batch at full size: 256 uneven vehicles (K
+    log-uniform in [1024, 32768], N in 30..150, 0..128 spheres, lambda = 1,
+    the benchmark's seed), one graph-replayed persistent launch in the shape
+    its batch autotuner picks (two samples per thread, block 128, 0.5 m
+    margin).  Every instance reports OK with finite outputs; a fixed sample
+    of them (the smallest and largest K, N, M and K N, and every 37th) is
+    compared with a full FP64 oracle step each, no value taken from the GPU."""
+    import os
+    import torch
+    probs = inp.batched_uneven(n=256, seed=2, dt=0.01)
+    cap = {"max_instances": 256, "max_samples": sum(p["params"]["K"] for p in probs), "N_max": 150, "M_max": 128}
+    s = M.Solver(probs[0]["model"], probs[0]["params"], cap)
+    s.set_shape(128, 1, 0, 0.5, 2)
+    insts = [_device(p, torch) for p in probs]
+    s.solve_batch(insts, graph=True)
+    torch.cuda.synchronize()
+    s.close()
+    got = [_host(d) for d in insts]
+    assert all(g["status"] == 0 for g in got)
+    assert all(np.isfinite(g[k]).all() for g in got for k in ("u_out", "u_cmd", "u_next", "x_next", "costs"))
+    K = np.array([p["params"]["K"] for p in probs])
+    N = np.array([p["params"]["N"] for p in probs])
+    Mo = np.array([p["obstacles"].shape[0] for p in probs])
+    pick = {int(K.argmin()), int(K.argmax()), int(N.argmin()), int(N.argmax()), int(Mo.argmax()),
+            int((K * N).argmax())} | set(range(0, 256, 37))
+    for i in sorted(pick):
+        ref = orc.mppi_step(probs[i], n_threads=os.cpu_count() or 1)
+        assert_step_close(probs[i], got[i], ref)
