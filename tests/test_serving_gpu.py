@@ -217,3 +217,55 @@ def test_default_shapes_large_batches_match_oracle(S, orc, inp):
         assert r["status"] == 0
         ref = orc.mppi_step(p, n_threads=8)
         assert control_err(r["u0"], ref["u_out"][0], p["params"]["sigma"]) <= U_RTOL
+
+
+def test_serving_fleet_full_size_sampled(S, orc, inp):
+    """The benchmark's serving workload at full size: 1000 vehicles (K in
+    {2048, 8192, 32768}, N in {50, 100}, 32 spheres each, lambda = 1), the
+    benchmark's server configuration (3 slots, batches of up to 2^21 samples
+    and 512 vehicles, default launch shapes), one request per vehicle, all
+    submitted at once.  Every request completes OK; a fixed sample of the
+    vehicles (the first of each (K, N) pair and every 97th) matches a full
+    FP64 oracle step: the command, the first updated control, and the
+    device-resident warm start and counter."""
+    import os
+    import time
+    fleet = inp.serving_fleet(n_vehicles=1000)
+    model, params = inp.model(motor_clip=1), inp.params()
+    srv = S.Server(model, params, {"max_vehicles": 1000, "slots": 3, "max_batch": 512, "N_max": 100, "M_max": 32,
+                                   "queue_capacity": 1024, "max_batch_samples": 1 << 21,
+                                   "hbm_budget_bytes": 64 << 30})
+    probs, vids, rids = [], [], []
+    for i, v in enumerate(fleet):
+        ref = inp.Trajectory("eight", {"phase": v["phase"]}).window(0.0, v["N"], v["dt"])
+        p = inp.params(K=v["K"], N=v["N"], dt=v["dt"], seed=v["seed"], stream_id=v["stream_id"],
+                       **{"lambda": 1.0, "sigma": (1.0, 1.0, 1.0, 0.5)})
+        prob = inp.problem(model, p, np.ascontiguousarray(ref[0]), ref, v["obstacles"], inp.hover_u(model, v["N"]),
+                           it=0)
+        probs.append(prob)
+        vids.append(srv.add_vehicle(v["K"], v["N"], v["dt"], 1.0, (1.0, 1.0, 1.0, 0.5), v["obstacles"],
+                                    prob["u_nom"], v["seed"], v["stream_id"]))
+    for vid, prob in zip(vids, probs):
+        rids.append(srv.submit(vid, prob["x_hat"], prob["ref"]))
+    assert all(r is not None for r in rids)
+    got, t0 = {}, time.time()
+    while len(got) < len(rids) and time.time() - t0 < 120:
+        for r in srv.poll():
+            got[r["request_id"]] = r
+    assert len(got) == len(rids)
+    assert all(r["status"] == 0 for r in got.values())
+    assert max(r["batch_size"] for r in got.values()) > 1
+    first = {}
+    for i, v in enumerate(fleet):
+        first.setdefault((v["K"], v["N"]), i)
+    pick = sorted(set(first.values()) | set(range(0, 1000, 97)))
+    for i in pick:
+        ref = orc.mppi_step(probs[i], n_threads=os.cpu_count() or 1)
+        r = got[rids[i]]
+        sig = probs[i]["params"]["sigma"]
+        assert control_err(r["u0"], ref["u_out"][0], sig) <= U_RTOL, i
+        assert control_err(r["u_cmd"], ref["u_cmd"], sig) <= U_RTOL, i
+        u_dev, it = srv.export_vehicle(vids[i])
+        assert it == 1
+        assert control_err(u_dev, ref["u_next"], sig) <= U_RTOL, i
+    srv.close()
